@@ -1,0 +1,198 @@
+"""CPU oracle for the checkerboard Metropolis method (arXiv 2502.18624).
+
+TEST INFRASTRUCTURE ONLY: tests/, the smoke check in __graft_entry__.py and
+the CPU-baseline leg of bench.py may import this package; the CUDA library
+and its Python binding never do.  The arithmetic lives in oracle.c (plain C,
+int8 spins, exact int64 sums); this module compiles it with gcc and wraps
+each function with numpy arrays.  See oracle.c for the passage each
+function restates and for what pins it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+ALWAYS = 1 << 32
+INIT_SWEEP = 0xFFFFFFFF
+TC_ISING = 2.0 / np.log(1.0 + np.sqrt(2.0))  # Onsager's critical temperature, J = 1
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into lib/liboracle.so with the host gcc."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library and return it."""
+    P = ctypes.c_void_p
+    u32, u64, i32, f64, sz = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                              ctypes.c_double, ctypes.c_size_t)
+    sig = {
+        "or_philox4x32_10": (None, [P, P, P]),
+        "or_philox_many": (None, [P, sz, P, P]),
+        "or_thresholds_ising": (None, [f64, f64, P]),
+        "or_thresholds_bc": (None, [f64, f64, f64, P]),
+        "or_init": (None, [i32, u32, u64, P]),
+        "or_sweep": (None, [i32, u32, u64, P, u32, P]),
+        "or_run": (None, [i32, u32, u64, P, u32, u32, P, P]),
+        "or_sweep_strip": (None, [i32, u32, u64, P, u32, u64, u32, P]),
+        "or_measure": (None, [i32, u32, P, P]),
+        "or_correlation": (None, [u32, P, u32, P, P]),
+        "or_sd_hist": (None, [u32, P, P]),
+        "or_pack": (None, [i32, u32, P, P]),
+        "or_hash_words": (u64, [P, u64]),
+        "or_hash": (u64, [i32, u32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def compile_variant(source_text: str, out_dir: str) -> str:
+    """Compile a modified copy of oracle.c (used by tests that plant mistakes)."""
+    src = os.path.join(out_dir, "oracle_variant.c")
+    lib = os.path.join(out_dir, "liboracle_variant.so")
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", src, "-o", lib, "-lm"])
+    return lib
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _key(seed: int) -> np.ndarray:
+    return np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one or many counters: ctr (...,4) uint32, key (2,)."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty_like(c)
+    _load().or_philox_many(_p(c), c.shape[0], _p(k), _p(out))
+    return out.reshape(np.shape(ctr))
+
+
+def thresholds(model: int, J: float, T: float, Delta: float = 0.0) -> np.ndarray:
+    """Integer acceptance table: 5 entries (Ising) or 54 (Blume-Capel)."""
+    if model == 0:
+        t = np.zeros(5, dtype=np.uint64)
+        _load().or_thresholds_ising(J, T, _p(t))
+    else:
+        t = np.zeros(54, dtype=np.uint64)
+        _load().or_thresholds_bc(J, Delta, T, _p(t))
+    return t
+
+
+def init(model: int, L: int, seed: int) -> np.ndarray:
+    s = np.zeros((L, L), dtype=np.int8)
+    _load().or_init(model, L, seed, _p(s))
+    return s
+
+
+def sweep(model: int, s: np.ndarray, seed: int, thr: np.ndarray, t: int) -> np.ndarray:
+    """One sweep (index t) in place; returns s."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    _load().or_sweep(model, s.shape[0], seed, _p(thr), t, _p(s))
+    return s
+
+
+def run(model: int, s: np.ndarray, seed: int, thr: np.ndarray, first: int, n: int,
+        record: bool = True):
+    """n sweeps from index `first` in place; returns (n,3) int64 (M, B, Q) per sweep."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    obs = np.zeros((n, 3), dtype=np.int64) if record else None
+    _load().or_run(model, s.shape[0], seed, _p(thr), first, n, _p(s),
+                   _p(obs) if record else None)
+    return obs
+
+
+def sweep_strip(model: int, L: int, seed: int, thr: np.ndarray, t: int, y0: int,
+                strip: np.ndarray) -> np.ndarray:
+    """Strip form of one sweep: strip holds rows y0-2..y0+H+1; rows 2..H+1 become exact."""
+    H = strip.shape[0] - 4
+    assert strip.shape == (H + 4, L) and strip.dtype == np.int8
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    _load().or_sweep_strip(model, L, seed, _p(thr), t, y0, H, _p(strip))
+    return strip
+
+
+def measure(model: int, s: np.ndarray) -> tuple[int, int, int]:
+    out = np.zeros(3, dtype=np.int64)
+    _load().or_measure(model, s.shape[0], _p(np.ascontiguousarray(s)), _p(out))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def correlation(s: np.ndarray, rmax: int) -> tuple[np.ndarray, np.ndarray]:
+    cx = np.zeros(rmax + 1, dtype=np.int64)
+    cy = np.zeros(rmax + 1, dtype=np.int64)
+    _load().or_correlation(s.shape[0], _p(np.ascontiguousarray(s)), rmax, _p(cx), _p(cy))
+    return cx, cy
+
+
+def sd_hist(s: np.ndarray) -> np.ndarray:
+    h = np.zeros(9, dtype=np.int64)
+    _load().or_sd_hist(s.shape[0], _p(np.ascontiguousarray(s)), _p(h))
+    return h
+
+
+def sd_value(hist: np.ndarray, J: float, T: float) -> float:
+    """Right-hand side of Eq. (3) from a sigma*h histogram."""
+    v = np.arange(-4, 5, dtype=np.float64)
+    n = float(hist.sum())
+    return float(np.sum(hist.astype(np.float64) * np.exp(-2.0 * J * v / T)) / n)
+
+
+def pack(model: int, s: np.ndarray) -> np.ndarray:
+    L = s.shape[0]
+    n = L * (L // 64) * (1 if model == 0 else 2)
+    w = np.zeros(n, dtype=np.uint64)
+    _load().or_pack(model, L, _p(np.ascontiguousarray(s)), _p(w))
+    return w
+
+
+def lattice_hash(model: int, s: np.ndarray) -> int:
+    return int(_load().or_hash(model, s.shape[0], _p(np.ascontiguousarray(s))))
+
+
+def hash_words(words: np.ndarray) -> int:
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    return int(_load().or_hash_words(_p(w), w.size))
+
+
+def energy(model: int, obs, J: float = 1.0, Delta: float = 0.0) -> float:
+    """E = -J B + Delta Q from exact (M, B, Q) integers (Eqs. (1)-(2))."""
+    _, B, Q = obs
+    return -J * float(B) + (Delta * float(Q) if model == 1 else 0.0)

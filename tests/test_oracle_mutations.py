@@ -1,0 +1,120 @@
+"""Show that the oracle's pins have power: plant a plausible mistake in a copy
+of oracle.c (compiled on the CPU, never on a GPU), and require that the pin
+meant to catch it fails.  Each entry names the mistake, the exact text it
+changes and the pin that must detect it.
+"""
+import contextlib
+import ctypes
+
+import numpy as np
+import pytest
+
+import physics as ph
+
+
+@contextlib.contextmanager
+def _variant(orc, tmp_path, old, new):
+    src = orc.source()
+    assert src.count(old) == 1, old
+    lib = orc._bind(ctypes.CDLL(orc.compile_variant(src.replace(old, new), str(tmp_path))))
+    saved = orc._lib
+    orc._lib = lib
+    try:
+        yield orc
+    finally:
+        orc._lib = saved
+
+
+def _ising_enum_fails(orc):
+    st = ph.ising_states(4)
+    exact, _ = ph.boltzmann_averages(st, 1.0, 0.0, ph.TC, 0)
+    thr = orc.thresholds(0, 1.0, ph.TC)
+    s = orc.init(0, 4, 5)
+    obs = orc.run(0, s, 5, thr, 0, 100_000)[1000:]
+    mean, err = ph.binned(-obs[:, 1].astype(np.float64))
+    return abs(mean - exact["E"]) > 4 * err
+
+
+def _bc_enum_fails(orc):
+    st = ph.bc_states(3)
+    exact, _ = ph.boltzmann_averages(st, 1.0, 1.0, 1.398, 1)
+    thr = orc.thresholds(1, 1.0, 1.398, 1.0)
+    s = orc.init(1, 3, 5)
+    obs = orc.run(1, s, 5, thr, 0, 100_000)[1000:]
+    E = -obs[:, 1].astype(np.float64) + obs[:, 2]
+    mean, err = ph.binned(E)
+    return abs(mean - exact["E"]) > 4 * err
+
+
+def _philox_fails(orc):
+    import test_oracle_philox as tp
+    lib = tp._curand()
+    ref = tp._host_stream(lib, 1234, 0, 4 * 64).reshape(64, 4)
+    ctr = np.stack([np.zeros(64), np.zeros(64), np.arange(64), np.zeros(64)], 1).astype(np.uint32)
+    return not np.array_equal(orc.philox(ctr, [1234, 0]), ref)
+
+
+def _measure_fails(orc):
+    s = np.where(np.random.default_rng(1).random((16, 16)) < 0.5, -1, 1).astype(np.int8)
+    return orc.measure(0, s)[1] != int(ph.bonds(s.astype(np.int64)))
+
+
+def _sd_fails(orc):
+    st = ph.ising_states(4)
+    _, w = ph.boltzmann_averages(st, 1.0, 0.0, ph.TC, 0)
+    rhs = np.array([orc.sd_value(orc.sd_hist(np.ascontiguousarray(x)), 1.0, ph.TC) for x in st])
+    return abs(float(w @ rhs) - 1.0) > 1e-9
+
+
+def _corr_fails(orc):
+    s = np.where(np.random.default_rng(2).random((32, 32)) < 0.5, -1, 1).astype(np.int8)
+    cx, cy = orc.correlation(s, 31)
+    f = np.fft.fft(s.astype(np.float64), axis=0)
+    ref = np.rint(np.fft.ifft(f * np.conj(f), axis=0).real.sum(axis=1)).astype(np.int64)
+    return not np.array_equal(cy, ref)
+
+
+def _thr_fails(orc):
+    import test_oracle_thresholds as tt
+    thr = orc.thresholds(0, 1.0, ph.TC)
+    return int(thr[3]) != tt._exact_thr(4.0, ph.TC) or int(thr[4]) != tt._exact_thr(8.0, ph.TC)
+
+
+def _init_fails(orc):
+    s = orc.init(1, 256, 9)
+    frac = np.array([(s == v).mean() for v in (-1, 0, 1)])
+    return np.max(np.abs(frac - 1 / 3)) > 0.01
+
+
+MUTATIONS = [
+    ("sweep drops the east neighbour",
+     "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
+     "s[y * L + (x + L - 1) % L];\n                s[site] = or_update_site", _ising_enum_fails),
+    ("Ising table indexed with the wrong sign", "thr[(sv * h + 4) / 2]", "thr[(-sv * h + 4) / 2]",
+     _ising_enum_fails),
+    ("Blume-Capel crystal-field term with the wrong sign",
+     "+ Delta * (double)(sp * sp - s * s)", "- Delta * (double)(sp * sp - s * s)", _bc_enum_fails),
+    ("Blume-Capel neighbour sum missing from dE",
+     "double dE = -J * (double)(sp - s) * (double)h +", "double dE = 0.0 * (double)h +", _bc_enum_fails),
+    ("Philox multipliers swapped", "#define OR_PHILOX_M0 0xD2511F53u", "#define OR_PHILOX_M0 0xCD9E8D57u",
+     _philox_fails),
+    ("Philox second key word never bumped", "k1 += OR_PHILOX_W1;", "k1 += 0;", _philox_fails),
+    ("Philox words 1 and 3 swapped", "c0 = n0; c1 = n1; c2 = n2; c3 = n3;", "c0 = n0; c1 = n3; c2 = n2; c3 = n1;",
+     _philox_fails),
+    ("bond sum misses vertical bonds", "B += v * s[((y + 1) % L) * L + x];", "", _measure_fails),
+    ("Schwinger-Dyson histogram with the wrong sign", "hist[s[y * L + x] * h + 4] += 1;",
+     "hist[-s[y * L + x] * h + 4] += 1;", _sd_fails),
+    ("correlation shifted by one extra row", "ay += v * s[((y + r) % L) * L + x];",
+     "ay += v * s[((y + r + 1) % L) * L + x];", _corr_fails),
+    ("threshold rounded up", "double v = floor(ldexp(exp(-dE / T), 32));",
+     "double v = ceil(ldexp(exp(-dE / T), 32));", _thr_fails),
+    ("Blume-Capel quench not uniform over three values", "(((uint64_t)w[0] * 3u) >> 32) - 1",
+     "(((uint64_t)w[0] * 2u) >> 32) - 1", _init_fails),
+]
+
+
+@pytest.mark.parametrize("name,old,new,detect", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(orc, tmp_path, name, old, new, detect):
+    assert not detect(orc), "the detector must pass on the unmodified oracle"
+    with _variant(orc, tmp_path, old, new) as bad:
+        assert detect(bad), f"planted mistake not detected: {name}"
