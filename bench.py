@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Throughput of the checkerboard Metropolis hot path on GB300.
+
+Workload (default): Ising, L = 2^17 (1.7e10 spins, 2 GiB packed), J = 1,
+T = Tc = 2/ln(1+sqrt 2), quench from seed 7, K sweeps (default 1000) with the
+exact (M, B, Q) after every sweep and C(r <= 1024) along both axes after
+sweeps 2^k.  A step is one sweep (two colour phases with the fused E/M
+reduction) plus its share of the correlation measurements.  The metric is
+attempted spin updates per nanosecond ("flips/ns", L^2 per sweep) over the
+whole job; the lattice is far larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload ising-tc|ising-0.9tc|ising-capacity|bc]
+
+N > 1 (torchrun, one process per GPU) runs independent replicas (seed + rank):
+the path has no exchange step, so there is no collective beyond the timing
+barrier and the max-over-ranks reduction.  --impl reference times the CPU
+oracle on the host on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin flips/ns on 1 GB300 (Ising L=2^17) + % of roofline; batched vs plain flips/ns"
+UNIT = "flips/ns"
+TC = 2.0 / math.log(1.0 + math.sqrt(2.0))
+# Integer issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one
+# 32-bit integer instruction per lane per clock).
+SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+# Algorithmic integer work of one Philox4x32-10 block: 10 rounds x
+# (2 widening 32x32 multiplies + 2 three-input XORs).
+OPS_PER_DRAW = 40
+
+WORKLOADS = {
+    "ising-tc": dict(model=0, L=1 << 17, T=TC, Delta=0.0, seed=7, rmax=1024,
+                     name="ising-2d L=131072 T=Tc seed=7: K sweeps, E/M every sweep, C(r<=1024) x/y at sweeps 2^k"),
+    "ising-0.9tc": dict(model=0, L=1 << 17, T=0.9 * TC, Delta=0.0, seed=7, rmax=1024,
+                        name="ising-2d L=131072 T=0.9Tc seed=7: K sweeps, E/M every sweep, C(r<=1024) at sweeps 2^k"),
+    "ising-capacity": dict(model=0, L=1 << 19, T=TC, Delta=0.0, seed=7, rmax=1024,
+                           name="ising-2d L=524288 (2^38 spins, 32 GiB) T=Tc seed=7: K sweeps, E/M every sweep"),
+    "bc": dict(model=1, L=1 << 16, T=1.398, Delta=1.0, seed=99, rmax=512,
+               name="blume-capel L=65536 Delta=1 T=1.398 seed=99: K sweeps, E/M/Q every sweep, C(r<=512) at sweeps 2^k"),
+}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job(updates_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job flips/ns: all ranks' updates over the slowest rank's time."""
+    return updates_per_rank * world / (max_seconds * 1e9)
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        return self
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(device_index).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[device_index]
+        return str(device_index)
+
+
+# ------------------------------------------------------------ native arm
+def powers_of_two_upto(k: int):
+    out, p = set(), 1
+    while p <= k:
+        out.add(p)
+        p *= 2
+    return out
+
+
+def run_job(lat, K: int, rmax: int, stream, with_corr: bool = True):
+    """K sweeps with per-sweep E/M and C(r) after sweeps 2^k; returns timing pieces.
+
+    Returns (sweep_ms_total, n_sweep_launches, total_draws, n_corr, obs_count).
+    CUDA events bracket every lat_sweep call on the lattice's stream, so the
+    sweep-kernel time is measured on the stream the kernels run on."""
+    import torch
+    meas = powers_of_two_upto(K) if with_corr else set()
+    done, sweep_ms, draws, ncorr, nobs = 0, 0.0, 0, 0, 0
+    while done < K:
+        nxt = min([m for m in meas if m > done], default=K)
+        n = min(nxt, K) - done
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        obs = lat.sweep(n)
+        e1.record(stream)
+        e1.synchronize()
+        sweep_ms += e0.elapsed_time(e1)
+        draws += int(obs["draws"].sum())
+        nobs += len(obs)
+        done += n
+        if done in meas:
+            lat.correlation(rmax)
+            ncorr += 1
+    return sweep_ms, 2 * K, draws, ncorr, nobs
+
+
+def native(args, wl):
+    import torch
+
+    from paper_2502_18624_gb300 import binding as b
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    b.load()
+    stream = torch.cuda.current_stream(device)
+    seed = wl["seed"] + rank
+    K, W = args.steps, args.warmup
+    mk = lambda: b.Lattice(wl["model"], wl["L"], wl["T"], seed, Delta=wl["Delta"], stream=stream, device=device)
+
+    # warm-up sweeps (kernels, module load, clocks), then a fresh quench for the timed job
+    lat = mk()
+    lat.sweep(W)
+    lat.close()
+    lat = mk()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    sampler = ClockSampler(gpu_id_for(local)).start()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    t_start.record(stream)
+    sweep_ms, nlaunch, draws, ncorr, _ = run_job(lat, K, wl["rmax"], stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(device)
+    clocks = sampler.stop()
+    barrier(dist, device)
+    secs = t_start.elapsed_time(t_end) / 1e3
+    max_secs = reduce_max(dist, secs, device)
+    L2 = float(wl["L"]) ** 2
+    value = whole_job(L2 * K, world, max_secs)
+    final_hash = lat.hash()
+    lat.close()
+
+    # end to end through the C ABI with host buffers: upload a quench from pinned
+    # memory, run the same job, download the final lattice.
+    lat = mk()
+    nbytes = b.lat_state_bytes(lat.params)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_np = host.numpy()
+    b.lat_get_state(lat.handle, nbytes, host_np)
+    lat.sweep_index = 0
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    t0 = time.perf_counter()
+    b.lat_set_state(lat.handle, host_np)
+    _, _, _, ncorr_e2e, nobs = run_job(lat, K, wl["rmax"], stream)
+    b.lat_get_state(lat.handle, nbytes, host_np)
+    torch.cuda.synchronize(device)
+    e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
+    assert lat.hash() == final_hash, "end-to-end run diverged from the device-resident run"
+    lat.close()
+    d2h = nbytes + nobs * 40 + ncorr_e2e * 2 * (wl["rmax"] + 1) * 8
+    e2e = {"value": whole_job(L2 * K, world, e2e_secs), "unit": UNIT,
+           "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
+
+    # roofline of the dominant kernel (the colour-phase sweep kernel)
+    launch_s = (sweep_ms / 1e3) / nlaunch
+    draws_per_launch = draws / nlaunch
+    achieved = OPS_PER_DRAW * draws_per_launch / launch_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tr = json.load(f)
+            if tr.get("workload") == args.workload and tr.get("kernel_rev") == kernel_rev():
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
+                "kernel": "k_ising_phase" if wl["model"] == 0 else "k_bc_phase",
+                "launch_ms": launch_s * 1e3, "draws_per_launch": draws_per_launch,
+                "ops_per_draw": OPS_PER_DRAW,
+                "peak_note": "integer issue peak 152 SM x 128 lanes x 2070 MHz (derived, not measured)",
+                "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": max_secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["name"].replace("K sweeps", "%d sweeps" % K), "L": wl["L"], "T": wl["T"],
+                       "Delta": wl["Delta"], "seed": wl["seed"], "rmax": wl["rmax"], "sweeps": K,
+                       "correlation_points": ncorr, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (packed lattice %d MiB vs 126 MiB L2), no flush" %
+                             (L2 / 8 / (1 << 20) * (1 if wl["model"] == 0 else 2))},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": nlaunch + 2 * ncorr, "clocks": clocks}
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def kernel_rev() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("k_sweep.cu", "philox.cuh", "lat_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2502_18624_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------ oracle (CPU)
+def oracle_strip_rate(wl, budget_s: float, H: int = 32):
+    """Time the unmodified oracle's strip sweep (one thread) on the workload's
+    lattice: a strip of H rows (+2 halo rows each side) of the quench.
+    Returns (flips_per_ns, sweeps_run, sites_per_sweep)."""
+    import oracle
+    oracle.build()
+    L = wl["L"]
+    thr = oracle.thresholds(wl["model"], 1.0, wl["T"], wl["Delta"])
+    strip = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, H + 4)
+    per_call = (H + 1) * L  # colour 0 on H+2 rows, colour 1 on H rows
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, n, 0, strip)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return per_call * n / (el * 1e9), n, per_call, el
+
+
+def cpu_baseline(wl, budget_s: float = 12.0):
+    rate, n, per_call, el = oracle_strip_rate(wl, budget_s)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d sweeps of a 32-row strip (+halo) of the L=%d lattice, one host thread, %.1f s" %
+                      (n, wl["L"], el)}
+
+
+def reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    L = wl["L"]
+    thr = oracle.thresholds(wl["model"], 1.0, wl["T"], wl["Delta"])
+    # size the strip so that warmup + steps end within about two minutes
+    probe = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, 5)
+    t0 = time.perf_counter()
+    oracle.sweep_strip(wl["model"], L, wl["seed"], thr, 0, 0, probe)
+    per_site = (time.perf_counter() - t0) / (2 * L)
+    steps_total = max(1, args.steps + args.warmup)
+    H = int(max(1, min(64, 120.0 / steps_total / (per_site * L) - 1)))
+    strip = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, H + 4)
+    for t in range(args.warmup):
+        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, t, 0, strip)
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, args.warmup + t, 0, strip)
+    el = time.perf_counter() - t0
+    value = (H + 1) * L * args.steps / (el * 1e9)
+    sample = "each step: one sweep of a %d-row strip (+2 halo rows each side) of the L=%d lattice" % (H, L)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8",
+            "data": "synthetic",
+            "config": {"workload": wl["name"].replace("K sweeps", "%d sweeps" % args.steps), "L": L, "T": wl["T"],
+                       "Delta": wl["Delta"], "seed": wl["seed"], "sample_rows": H},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ising-tc")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference(args, wl)
+    else:
+        native(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * lat.h -- C ABI of the GB300 (sm_103a) checkerboard Metropolis library for
+ * the 2D Ising and Blume-Capel models (Bisson et al., arXiv 2502.18624).
+ *
+ * The problem (section "Nature of problem", section 2): an L x L square
+ * lattice with periodic boundaries, Hamiltonian Eq. (1) (Ising, s = +-1) or
+ * Eq. (2) (Blume-Capel, s in {-1, 0, +1}), evolved by single-spin-flip
+ * Metropolis dynamics (section 1) in checkerboard order: every sweep updates
+ * the sites with x+y even (colour 0), then those with x+y odd (colour 1)
+ * (section 3.1).  Measurements are the exact integer sums behind the energy
+ * and magnetisation, and the spin-spin correlation from every site along
+ * both axes (section 3.3).
+ *
+ * Random stream.  Every decision draws Philox4x32-10 (section 3.2) with
+ * key = (seed low 32 bits, seed high 32 bits) and counter
+ * (site low 32 bits, site high 32 bits, sweep index, colour), site = y*L + x.
+ * The initial quench uses sweep index 0xFFFFFFFF and colour 0.  Ising: a
+ * site with dE = 2 J s h <= 0 flips; otherwise it flips iff word 0 < thr[dE].
+ * Blume-Capel: every site draws; the low bit of word 1 picks the proposal
+ * among the two other values in ascending order, and the move is accepted
+ * iff dE <= 0 or word 0 < thr.  thr = floor(2^32 exp(-dE/T)), built once in
+ * FP64 on the host.  Because the stream is counter-based and same-colour
+ * sites share no bond, every result is independent of launch shape, tiling
+ * and batching.
+ *
+ * Conventions for every call:
+ *   - return 0 (LAT_OK) on success or a negative LAT_E* code; no call throws.
+ *   - handles are not thread-safe; one handle is used by one host thread.
+ *   - device work is ordered on the handle's CUDA stream; calls that return
+ *     host data synchronise that stream before returning.
+ *   - there is no CPU fallback: without a usable CUDA device the calls that
+ *     need one return LAT_ECUDA.
+ */
+#ifndef LAT_H
+#define LAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define LAT_OK 0
+#define LAT_EINVAL (-1)    /* bad argument (see each call) */
+#define LAT_ENOMEM (-2)    /* device buffer too small, or allocation failed */
+#define LAT_ECUDA (-3)     /* a CUDA call failed (no device, launch error, ...) */
+#define LAT_ETIMEDOUT (-4) /* a bounded device-side wait gave up */
+#define LAT_ESTATE (-5)    /* handle in the wrong state for this call */
+
+/* Models. */
+#define LAT_ISING 0
+#define LAT_BLUME_CAPEL 1
+
+/* Largest accepted linear size: 2^20 (2^40 spins, 128 GiB as Ising). */
+#define LAT_MAX_L (1u << 20)
+
+typedef struct lat lat_t; /* opaque; owned by the library */
+
+/* Simulation parameters (Eqs. (1)-(2); section 2).
+ *   model  LAT_ISING or LAT_BLUME_CAPEL.
+ *   L      linear size, a multiple of 64, 64 <= L <= LAT_MAX_L.
+ *   J      ferromagnetic coupling, J > 0 (section 2 takes J > 0).
+ *   Delta  crystal-field coupling of Eq. (2); ignored for Ising.
+ *   T      temperature, T > 0 (k_B = 1).
+ *   seed   64-bit key of the random stream. */
+typedef struct {
+    int32_t model;
+    uint32_t L;
+    double J;
+    double Delta;
+    double T;
+    uint64_t seed;
+} lat_params;
+
+/* Exact observables after a sweep (Eqs. (1)-(2)):
+ *   M = sum of s, B = sum over nearest-neighbour bonds (each once) of s s',
+ *   Q = sum of s^2, so that E = -J B + Delta Q (Delta term for BC only).
+ *   sweep = number of sweeps completed on the lattice when measured.
+ *   draws = Philox blocks drawn during that sweep (both colours): the
+ *   uphill Ising sites whose threshold is neither 0 nor 2^32, or every
+ *   Blume-Capel site (L^2).  A work count, not an observable; 0 from
+ *   lat_measure. */
+typedef struct {
+    int64_t M;
+    int64_t B;
+    int64_t Q;
+    uint64_t sweep;
+    uint64_t draws;
+} lat_obs;
+
+/* Device bytes lat_create needs for these parameters: the packed lattice
+ * (L*L/8 bytes Ising, L*L/4 bytes Blume-Capel) plus a small workspace for
+ * per-sweep observables, correlation sums and a transfer stage.
+ * Returns 0 if the parameters are invalid.  Host only; needs no GPU. */
+size_t lat_footprint(const lat_params* p);
+
+/* The acceptance table the library builds for p (section 3.2: flip
+ * probabilities e^{-4 beta}, e^{-8 beta} or 1 for Ising; Eq. (2) for BC),
+ * written to out[0..n).  Entries are 2^32 for "always accept" (dE <= 0),
+ * else floor(2^32 exp(-dE/T)).  Ising: 5 entries, entry i for the product
+ * s*h = 2i - 4.  Blume-Capel: 54 entries, entry ((s+1)*2 + b)*9 + (h+4)
+ * for the move from s to the b-th other value (ascending) with neighbour
+ * sum h.  n must be >= 5 (Ising) or >= 54 (BC), else LAT_EINVAL.  Host only. */
+int lat_thresholds(const lat_params* p, uint64_t* out, size_t n);
+
+/* Create a lattice and draw its initial quench (infinite-temperature start,
+ * section 1) on the device.
+ *   dev_buf  caller-owned device memory of at least lat_footprint(p) bytes,
+ *            256-byte aligned, that outlives the handle; or NULL to let the
+ *            library cudaMalloc (and later free) its own buffer.
+ *   bytes    size of dev_buf (ignored when dev_buf is NULL).
+ *   stream   cudaStream_t to order all of this handle's work on (NULL = the
+ *            legacy default stream).
+ *   out      receives the handle.
+ * Errors: LAT_EINVAL (bad params: L not a multiple of 64, L < 64 or
+ * L > LAT_MAX_L, J <= 0, T <= 0, model unknown, NULL out, misaligned
+ * dev_buf), LAT_ENOMEM (bytes < lat_footprint or allocation failure),
+ * LAT_ECUDA.  The quench is enqueued, not synchronised. */
+int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, lat_t** out);
+
+/* Run nsweeps checkerboard sweeps (section 3.1), with sweep indices
+ * next .. next+nsweeps-1 where next = lat_sweep_index().  When per_sweep is
+ * not NULL it receives nsweeps host records: the exact (M, B, Q) after each
+ * sweep, computed on the device inside the colour-1 phase.  Sweep indices
+ * must stay below 0xFFFFFFFF (reserved for the quench): LAT_EINVAL otherwise.
+ * Synchronises the stream only when per_sweep is not NULL. */
+int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep);
+
+/* Exact (M, B, Q) of the current lattice by a separate reduction kernel
+ * (an independent check of the fused per-sweep values).  Synchronises. */
+int lat_measure(lat_t* h, lat_obs* out);
+
+/* Spin-spin correlation from every site along both axes (section 3.3,
+ * all sources, every distance): cx[r] = sum_{x,y} s(x,y) s(x+r,y) and
+ * cy[r] = sum_{x,y} s(x,y) s(x,y+r), periodic, r = 0..rmax, exact int64
+ * raw sums (no mean subtracted, no normalisation).  cx and cy are host
+ * arrays of rmax+1 entries.  rmax must be <= L/2 (LAT_EINVAL).  Synchronises. */
+int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy);
+
+/* Schwinger-Dyson histogram of Eq. (3): hist[v+4] = number of sites with
+ * s_x * h_x = v, v = -4..4, h_x the sum of the four neighbours.  Eq. (3)'s
+ * right-hand side is L^-2 sum_v hist[v+4] exp(-2 J v / T).  hist is a host
+ * array of 9 entries.  Synchronises. */
+int lat_sd_hist(lat_t* h, int64_t* hist);
+
+/* Canonical lattice hash: sum over canonical words i of
+ * mix(i XOR word_i) mod 2^64, mix the SplitMix64 finaliser.  Canonical
+ * words: W = L/64 per row, bit b of word (y, j) is site x = 64j + b; Ising
+ * one plane (bit set iff s = +1); Blume-Capel plane 0 (bit set iff s != 0)
+ * at words 0..L*W-1 then plane 1 (bit set iff s = -1).  Synchronises. */
+int lat_hash(lat_t* h, uint64_t* out);
+
+/* Copy the whole lattice to host int8 values (L*L bytes, row-major,
+ * s[y*L + x]).  Synchronises. */
+int lat_get_spins(lat_t* h, int8_t* host_out);
+
+/* Copy nrows rows starting at row y0 (wrapping modulo L) to host int8
+ * (nrows*L bytes).  y0 < L and nrows <= L, else LAT_EINVAL.  Synchronises. */
+int lat_get_rows(lat_t* h, uint32_t y0, uint32_t nrows, int8_t* host_out);
+
+/* Replace the lattice with host int8 values (L*L bytes, -1/+1 for Ising,
+ * -1/0/+1 for Blume-Capel; any other value gives LAT_EINVAL and leaves the
+ * lattice unspecified).  Does not change the sweep index.  Synchronises. */
+int lat_set_spins(lat_t* h, const int8_t* host_in);
+
+/* Bytes of the packed device state (the lattice alone). */
+size_t lat_state_bytes(const lat_params* p);
+
+/* Raw packed state to/from host memory (checkpointing).  Layout: Ising,
+ * L rows of L/64 little-endian uint64 words, bit b of word j = site 64j+b,
+ * set iff s = +1; Blume-Capel, L rows of L/64 word pairs (plane n: s != 0,
+ * plane g: s = -1), pair j covering sites 64j..64j+63.  bytes must equal
+ * lat_state_bytes.  Host memory may be pinned or pageable.  Synchronises. */
+int lat_get_state(lat_t* h, void* host, size_t bytes);
+int lat_set_state(lat_t* h, const void* host, size_t bytes);
+
+/* Number of sweeps completed (the index of the next sweep), and its setter
+ * for resuming from a checkpoint (must be < 0xFFFFFFFF). */
+int lat_get_sweep_index(lat_t* h, uint64_t* next);
+int lat_set_sweep_index(lat_t* h, uint64_t next);
+
+/* The acceptance table in use by this handle (see lat_thresholds). */
+int lat_get_thresholds(lat_t* h, uint64_t* out, size_t n);
+
+/* Release the handle (and the buffer, if the library allocated it).
+ * Synchronises the stream first.  NULL is accepted. */
+int lat_destroy(lat_t* h);
+
+/* Static description of an error code. */
+const char* lat_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAT_H */

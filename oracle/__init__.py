@@ -48,6 +48,7 @@ def _bind(lib):
         "or_thresholds_ising": (None, [f64, f64, P]),
         "or_thresholds_bc": (None, [f64, f64, f64, P]),
         "or_init": (None, [i32, u32, u64, P]),
+        "or_init_rows": (None, [i32, u32, u64, u64, u32, P]),
         "or_sweep": (None, [i32, u32, u64, P, u32, P]),
         "or_run": (None, [i32, u32, u64, P, u32, u32, P, P]),
         "or_sweep_strip": (None, [i32, u32, u64, P, u32, u64, u32, P]),
@@ -119,6 +120,13 @@ def thresholds(model: int, J: float, T: float, Delta: float = 0.0) -> np.ndarray
 def init(model: int, L: int, seed: int) -> np.ndarray:
     s = np.zeros((L, L), dtype=np.int8)
     _load().or_init(model, L, seed, _p(s))
+    return s
+
+
+def init_rows(model: int, L: int, seed: int, y0: int, nrows: int) -> np.ndarray:
+    """Rows y0..y0+nrows-1 (mod L) of the quench, shape (nrows, L)."""
+    s = np.zeros((nrows, L), dtype=np.int8)
+    _load().or_init_rows(model, L, seed, y0, nrows, _p(s))
     return s
 
 

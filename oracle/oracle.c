@@ -155,6 +155,25 @@ void or_init(int model, uint32_t L, uint64_t seed, int8_t* s)
         }
 }
 
+/* The same quench for rows y0 .. y0+nrows-1 (mod L) only, into an          */
+/* nrows x L array: used to check lattices too large to hold as int8.       */
+void or_init_rows(int model, uint32_t L, uint64_t seed, uint64_t y0, uint32_t nrows, int8_t* s)
+{
+    for (uint64_t r = 0; r < nrows; ++r) {
+        uint64_t y = (y0 + r) % L;
+        for (uint64_t x = 0; x < L; ++x) {
+            uint32_t w[4];
+            or_draw(seed, y * L + x, OR_INIT_SWEEP, 0, w);
+            int8_t v;
+            if (model == 0)
+                v = (w[0] >> 31) ? 1 : -1;
+            else
+                v = (int8_t)((int)(((uint64_t)w[0] * 3u) >> 32) - 1);
+            s[r * L + x] = v;
+        }
+    }
+}
+
 /* One Metropolis decision for the spin value sv with neighbour sum h at the  */
 /* given site, during sweep `sweep` and colour phase `colour`.                */
 static int8_t or_update_site(int model, int sv, int h, uint64_t site, uint32_t sweep, uint32_t colour,

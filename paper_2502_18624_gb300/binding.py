@@ -1,0 +1,285 @@
+"""ctypes binding of include/lat.h: the same entry-point names, argument
+marshalling only.  Every step of the simulation runs in liblat.so's CUDA
+kernels; if the library is missing or cannot be built this module raises, it
+never falls back to anything else.
+
+PyTorch is used only for device memory (a uint8 tensor handed to lat_create
+as the caller-owned buffer) and for streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LAT_OK, LAT_EINVAL, LAT_ENOMEM, LAT_ECUDA, LAT_ETIMEDOUT, LAT_ESTATE = 0, -1, -2, -3, -4, -5
+LAT_ISING, LAT_BLUME_CAPEL = 0, 1
+LAT_MAX_L = 1 << 20
+TC_ISING = 2.0 / np.log(1.0 + np.sqrt(2.0))
+
+
+class LatError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+class lat_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("L", ctypes.c_uint32), ("J", ctypes.c_double),
+                ("Delta", ctypes.c_double), ("T", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class lat_obs(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("B", ctypes.c_int64), ("Q", ctypes.c_int64),
+                ("sweep", ctypes.c_uint64), ("draws", ctypes.c_uint64)]
+
+
+OBS_DTYPE = np.dtype([("M", np.int64), ("B", np.int64), ("Q", np.int64), ("sweep", np.uint64),
+                      ("draws", np.uint64)])
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblat.so (building it first if needed); raise if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("liblat.so is missing (%s); run build()" % _build.LIB)
+    lib = ctypes.CDLL(_build.LIB)
+    P, sz, u32, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    PP = ctypes.POINTER(lat_params)
+    sigs = {
+        "lat_footprint": (sz, [PP]),
+        "lat_state_bytes": (sz, [PP]),
+        "lat_thresholds": (i32, [PP, P, sz]),
+        "lat_create": (i32, [PP, P, sz, P, ctypes.POINTER(P)]),
+        "lat_sweep": (i32, [P, u32, P]),
+        "lat_measure": (i32, [P, P]),
+        "lat_correlation": (i32, [P, u32, P, P]),
+        "lat_sd_hist": (i32, [P, P]),
+        "lat_hash": (i32, [P, P]),
+        "lat_get_spins": (i32, [P, P]),
+        "lat_get_rows": (i32, [P, u32, u32, P]),
+        "lat_set_spins": (i32, [P, P]),
+        "lat_get_state": (i32, [P, P, sz]),
+        "lat_set_state": (i32, [P, P, sz]),
+        "lat_get_sweep_index": (i32, [P, P]),
+        "lat_set_sweep_index": (i32, [P, u64]),
+        "lat_get_thresholds": (i32, [P, P, sz]),
+        "lat_destroy": (i32, [P]),
+        "lat_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, what: str) -> None:
+    if code != LAT_OK:
+        raise LatError(code, what)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(model: int, L: int, T: float, seed: int, J: float = 1.0, Delta: float = 0.0) -> lat_params:
+    return lat_params(int(model), int(L), float(J), float(Delta), float(T), int(seed) & (2**64 - 1))
+
+
+def strerror(code: int) -> str:
+    return load().lat_strerror(code).decode()
+
+
+# ---- entry points with the C names -----------------------------------------
+
+def lat_footprint(p: lat_params) -> int:
+    return int(load().lat_footprint(ctypes.byref(p)))
+
+
+def lat_state_bytes(p: lat_params) -> int:
+    return int(load().lat_state_bytes(ctypes.byref(p)))
+
+
+def lat_thresholds(p: lat_params) -> np.ndarray:
+    out = np.zeros(54, dtype=np.uint64)
+    _check(load().lat_thresholds(ctypes.byref(p), _ptr(out), out.size), "lat_thresholds")
+    return out[: (5 if p.model == LAT_ISING else 54)].copy()
+
+
+def lat_create(p: lat_params, dev_buf: int | None, nbytes: int, stream: int | None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lat_create(ctypes.byref(p), dev_buf, nbytes, stream, ctypes.byref(h)), "lat_create")
+    return h
+
+
+def lat_sweep(h, nsweeps: int, record: bool = True):
+    obs = np.zeros(nsweeps, dtype=OBS_DTYPE) if record else None
+    _check(load().lat_sweep(h, nsweeps, _ptr(obs) if record and nsweeps else None), "lat_sweep")
+    return obs
+
+
+def lat_measure(h) -> tuple[int, int, int, int]:
+    o = lat_obs()
+    _check(load().lat_measure(h, ctypes.byref(o)), "lat_measure")
+    return o.M, o.B, o.Q, o.sweep
+
+
+def lat_correlation(h, rmax: int) -> tuple[np.ndarray, np.ndarray]:
+    cx = np.zeros(rmax + 1, dtype=np.int64)
+    cy = np.zeros(rmax + 1, dtype=np.int64)
+    _check(load().lat_correlation(h, rmax, _ptr(cx), _ptr(cy)), "lat_correlation")
+    return cx, cy
+
+
+def lat_sd_hist(h) -> np.ndarray:
+    out = np.zeros(9, dtype=np.int64)
+    _check(load().lat_sd_hist(h, _ptr(out)), "lat_sd_hist")
+    return out
+
+
+def lat_hash(h) -> int:
+    out = np.zeros(1, dtype=np.uint64)
+    _check(load().lat_hash(h, _ptr(out)), "lat_hash")
+    return int(out[0])
+
+
+def lat_get_spins(h, L: int) -> np.ndarray:
+    out = np.empty((L, L), dtype=np.int8)
+    _check(load().lat_get_spins(h, _ptr(out)), "lat_get_spins")
+    return out
+
+
+def lat_get_rows(h, L: int, y0: int, nrows: int) -> np.ndarray:
+    out = np.empty((nrows, L), dtype=np.int8)
+    _check(load().lat_get_rows(h, y0, nrows, _ptr(out)), "lat_get_rows")
+    return out
+
+
+def lat_set_spins(h, s: np.ndarray) -> None:
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    _check(load().lat_set_spins(h, _ptr(s)), "lat_set_spins")
+
+
+def lat_get_state(h, nbytes: int, out: np.ndarray | None = None) -> np.ndarray:
+    out = np.empty(nbytes, dtype=np.uint8) if out is None else out
+    _check(load().lat_get_state(h, _ptr(out), nbytes), "lat_get_state")
+    return out
+
+
+def lat_set_state(h, state: np.ndarray) -> None:
+    state = np.ascontiguousarray(state).view(np.uint8)
+    _check(load().lat_set_state(h, _ptr(state), state.nbytes), "lat_set_state")
+
+
+def lat_get_sweep_index(h) -> int:
+    v = ctypes.c_uint64()
+    _check(load().lat_get_sweep_index(h, ctypes.byref(v)), "lat_get_sweep_index")
+    return v.value
+
+
+def lat_set_sweep_index(h, t: int) -> None:
+    _check(load().lat_set_sweep_index(h, t), "lat_set_sweep_index")
+
+
+def lat_get_thresholds(h, model: int) -> np.ndarray:
+    out = np.zeros(54, dtype=np.uint64)
+    _check(load().lat_get_thresholds(h, _ptr(out), out.size), "lat_get_thresholds")
+    return out[: (5 if model == LAT_ISING else 54)].copy()
+
+
+def lat_destroy(h) -> None:
+    _check(load().lat_destroy(h), "lat_destroy")
+
+
+# ---- convenience wrapper over torch device memory ---------------------------
+
+class Lattice:
+    """One lattice on the current CUDA device, in a torch-owned buffer."""
+
+    def __init__(self, model: int, L: int, T: float, seed: int, J: float = 1.0, Delta: float = 0.0,
+                 stream=None, device=None):
+        import torch
+
+        self.params = make_params(model, L, T, seed, J, Delta)
+        self.model, self.L = int(model), int(L)
+        nbytes = lat_footprint(self.params)
+        if nbytes == 0:
+            raise LatError(LAT_EINVAL, "lat_footprint")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.handle = lat_create(self.params, self.buffer.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def sweep(self, n: int, record: bool = True):
+        return lat_sweep(self.handle, n, record)
+
+    def measure(self):
+        return lat_measure(self.handle)
+
+    def correlation(self, rmax: int):
+        return lat_correlation(self.handle, rmax)
+
+    def sd_hist(self):
+        return lat_sd_hist(self.handle)
+
+    def hash(self) -> int:
+        return lat_hash(self.handle)
+
+    def spins(self) -> np.ndarray:
+        return lat_get_spins(self.handle, self.L)
+
+    def rows(self, y0: int, nrows: int) -> np.ndarray:
+        return lat_get_rows(self.handle, self.L, y0, nrows)
+
+    def set_spins(self, s: np.ndarray) -> None:
+        lat_set_spins(self.handle, s)
+
+    def state(self) -> np.ndarray:
+        return lat_get_state(self.handle, lat_state_bytes(self.params))
+
+    def set_state(self, st: np.ndarray) -> None:
+        lat_set_state(self.handle, st)
+
+    @property
+    def sweep_index(self) -> int:
+        return lat_get_sweep_index(self.handle)
+
+    @sweep_index.setter
+    def sweep_index(self, t: int) -> None:
+        lat_set_sweep_index(self.handle, t)
+
+    def thresholds(self) -> np.ndarray:
+        return lat_get_thresholds(self.handle, self.model)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lat_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

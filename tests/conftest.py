@@ -19,3 +19,14 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """A CUDA device is required: GPU tests fail, never skip, without one."""
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    torch.cuda.init()
+    from paper_2502_18624_gb300 import binding
+    binding.load()
+    return torch.device("cuda", 0)

@@ -1,0 +1,100 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+symbol include/*.h declares, its host-only calls work, and the calls that
+need a device fail with LAT_ECUDA instead of computing anything on the CPU.
+The acceptance table it builds (its own FP64 code) equals the oracle's bit
+for bit over the workload parameter ranges.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2502_18624_gb300 import binding as b
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("lat_") and not name.endswith("_t"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(b.load().__dict__["_name"])
+    names = _declared_functions()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm103a():
+    # The build passes exactly one -gencode for sm_103a.
+    from paper_2502_18624_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(_build.LIB)
+
+
+@pytest.mark.parametrize("model,L,J,T,Delta", [
+    (0, 64, 1.0, 1.0, 0.0), (1, 64, 1.0, 1.0, 0.0),
+    (0, 100, 1.0, 1.0, 0.0), (0, 32, 1.0, 1.0, 0.0), (0, 0, 1.0, 1.0, 0.0),
+    (0, (1 << 20) + 64, 1.0, 1.0, 0.0), (1, 1 << 20, 1.0, 1.0, 0.0),
+    (0, 64, 0.0, 1.0, 0.0), (0, 64, -1.0, 1.0, 0.0), (0, 64, 1.0, 0.0, 0.0), (0, 64, 1.0, -2.0, 0.0),
+    (2, 64, 1.0, 1.0, 0.0), (0, 64, float("nan"), 1.0, 0.0), (1, 64, 1.0, 1.0, float("inf")),
+])
+def test_parameter_validation(model, L, J, T, Delta):
+    p = b.make_params(model, L, T, 1, J, Delta)
+    valid = model in (0, 1) and L >= 64 and L % 64 == 0 and J > 0 and T > 0 and np.isfinite(J) \
+        and np.isfinite(Delta) and L <= (1 << 20) and not (model == 1 and L > (1 << 19))
+    assert (b.lat_footprint(p) > 0) == valid
+    if not valid:
+        with pytest.raises(b.LatError) as e:
+            b.lat_thresholds(p)
+        assert e.value.code == b.LAT_EINVAL
+
+
+def test_footprint_covers_the_packed_lattice():
+    for model, L in [(0, 64), (0, 1 << 17), (0, 1 << 19), (1, 1 << 16), (1, 192)]:
+        p = b.make_params(model, L, 1.0, 1)
+        state = b.lat_state_bytes(p)
+        assert state == L * L // (8 if model == 0 else 4)
+        assert state <= b.lat_footprint(p) <= state + (6 << 20) + 16 * L
+
+
+def test_device_calls_fail_loudly_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = b.make_params(0, 256, b.TC_ISING, 1234)
+    with pytest.raises(b.LatError) as e:
+        b.lat_create(p, None, 0, None)
+    assert e.value.code == b.LAT_ECUDA
+
+
+def _cases():
+    rng = np.random.default_rng(2025)
+    cases = [(0, 1.0, b.TC_ISING, 0.0), (0, 1.0, 0.9 * b.TC_ISING, 0.0), (0, 1.0, 2.269185, 0.0),
+             (1, 1.0, 1.398, 1.0), (1, 1.0, 1.69, 0.5), (1, 1.0, 1.69, 1.5), (1, 1.0, 0.608, 1.966),
+             (0, 1.0, 1e-3, 0.0), (0, 1.0, 1e15, 0.0), (1, 1.0, 1e-3, 1.0), (1, 0.7, 2.5, -0.3)]
+    for _ in range(40):
+        cases.append((0, 1.0, float(rng.uniform(0.8, 1.2) * 2.269185), 0.0))
+        cases.append((1, 1.0, float(rng.uniform(1.2, 1.6)), 1.0))
+        cases.append((1, 1.0, float(rng.uniform(0.7, 1.3) * 1.69), float(rng.choice([0.5, 1.5]))))
+    return cases
+
+
+def test_thresholds_equal_the_oracle_bit_for_bit(orc):
+    for model, J, T, Delta in _cases():
+        p = b.make_params(model, 64, T, 1, J, Delta)
+        lib = b.lat_thresholds(p)
+        ref = orc.thresholds(model, J, T, Delta)
+        assert np.array_equal(lib, ref), (model, J, T, Delta)

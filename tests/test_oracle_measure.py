@@ -111,3 +111,12 @@ def test_strip_sweep_equals_full_sweep(orc, model, Delta):
         strip = np.ascontiguousarray(s[rows])
         orc.sweep_strip(model, L, seed, thr, t, y0, strip)
         assert np.array_equal(strip[2:H + 2], full[[(y0 + i) % L for i in range(H)]])
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_init_rows_equals_full_init(orc, model):
+    L, seed = 128, 77
+    full = orc.init(model, L, seed)
+    for y0, n in [(0, 5), (100, 40), (127, 1)]:
+        part = orc.init_rows(model, L, seed, y0, n)
+        assert np.array_equal(part, full[[(y0 + i) % L for i in range(n)]])

@@ -108,8 +108,9 @@ MUTATIONS = [
      "ay += v * s[((y + r + 1) % L) * L + x];", _corr_fails),
     ("threshold rounded up", "double v = floor(ldexp(exp(-dE / T), 32));",
      "double v = ceil(ldexp(exp(-dE / T), 32));", _thr_fails),
-    ("Blume-Capel quench not uniform over three values", "(((uint64_t)w[0] * 3u) >> 32) - 1",
-     "(((uint64_t)w[0] * 2u) >> 32) - 1", _init_fails),
+    ("Blume-Capel quench not uniform over three values",
+     "s[site] = (int8_t)((int)(((uint64_t)w[0] * 3u) >> 32) - 1);",
+     "s[site] = (int8_t)((int)(((uint64_t)w[0] * 2u) >> 32) - 1);", _init_fails),
 ]
 
 
