@@ -233,25 +233,10 @@ def native(args, wl):
 
     # end to end through the C ABI with host buffers: upload a quench from pinned
     # memory, run the same job, download the final lattice.
-    lat = mk()
-    nbytes = b.lat_state_bytes(lat.params)
-    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    host_np = host.numpy()
-    b.lat_get_state(lat.handle, nbytes, host_np)
-    lat.sweep_index = 0
-    torch.cuda.synchronize(device)
-    barrier(dist, device)
-    t0 = time.perf_counter()
-    b.lat_set_state(lat.handle, host_np)
-    _, _, _, ncorr_e2e, nobs = run_job(lat, K, wl["rmax"], stream)
-    b.lat_get_state(lat.handle, nbytes, host_np)
-    torch.cuda.synchronize(device)
-    e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
-    assert lat.hash() == final_hash, "end-to-end run diverged from the device-resident run"
-    lat.close()
-    d2h = nbytes + nobs * 40 + ncorr_e2e * 2 * (wl["rmax"] + 1) * 8
-    e2e = {"value": whole_job(L2 * K, world, e2e_secs), "unit": UNIT,
-           "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash)
+    line_e2e = e2e
 
     # roofline of the dominant kernel (the colour-phase sweep kernel)
     launch_s = (sweep_ms / 1e3) / nlaunch
@@ -274,7 +259,35 @@ def native(args, wl):
                 "ops_per_draw": OPS_PER_DRAW,
                 "peak_note": "integer issue peak 152 SM x 128 lanes x 2070 MHz (derived, not measured)",
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
+    return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist)
 
+
+def end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash):
+    import torch
+    lat = mk()
+    nbytes = b.lat_state_bytes(lat.params)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_np = host.numpy()
+    b.lat_get_state(lat.handle, nbytes, host_np)
+    lat.sweep_index = 0
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    t0 = time.perf_counter()
+    b.lat_set_state(lat.handle, host_np)
+    _, _, _, ncorr_e2e, nobs = run_job(lat, K, wl["rmax"], stream)
+    b.lat_get_state(lat.handle, nbytes, host_np)
+    torch.cuda.synchronize(device)
+    e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
+    assert lat.hash() == final_hash, "end-to-end run diverged from the device-resident run"
+    lat.close()
+    d2h = nbytes + nobs * 40 + ncorr_e2e * 2 * (wl["rmax"] + 1) * 8
+    L2 = float(wl["L"]) ** 2
+    return {"value": whole_job(L2 * K, world, e2e_secs), "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
+
+
+def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, e2e, clocks, dist):
+    L2 = float(wl["L"]) ** 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": max_secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -285,7 +298,8 @@ def native(args, wl):
                              (L2 / 8 / (1 << 20) * (1 if wl["model"] == 0 else 2))},
             "roofline": roofline, "e2e": e2e, "gpu_launches": nlaunch + 2 * ncorr, "clocks": clocks}
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+        if args.cpu_seconds > 0:
+            line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -379,9 +393,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ising-tc")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="oracle CPU-baseline budget; 0 skips it (profiling runs)")
+    ap.add_argument("--L", type=int, default=None, help="override the linear size (small profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args(argv)
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.L:
+        wl["L"] = args.L
+        wl["rmax"] = min(wl["rmax"], args.L // 2)
+        wl["name"] = wl["name"].replace("L=%d" % WORKLOADS[args.workload]["L"], "L=%d" % args.L)
     if args.impl == "reference":
         reference(args, wl)
     else:

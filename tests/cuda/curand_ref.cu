@@ -1,8 +1,10 @@
 // curand_ref.cu -- test helper: Philox4_32_10 outputs from cuRAND's device
 // API for arbitrary counters, to pin the oracle's generator on all four
-// counter words.  curand_init(seed, subsequence, offset) with
-// subsequence = c2 | c3 << 32 and offset = 4 (c0 | c1 << 32) positions the
-// generator at counter (c0, c1, c2, c3); curand4 then returns its 4 words.
+// counter words.  curand_init(seed, subsequence = c2 | c3 << 32, 0) sets the
+// upper counter words; skipping 4n elements advances words 0-1 by n blocks,
+// done in four steps of 4 (n >> 2) plus 4 (n & 3) so that no element count
+// overflows 64 bits.  curand4 then returns the 4 words at counter
+// (c0, c1, c2, c3).
 #include <cuda_runtime.h>
 #include <curand_kernel.h>
 
@@ -16,7 +18,9 @@ __global__ void k_ref(const uint4* ctr, size_t n, unsigned long long seed, uint4
     curandStatePhilox4_32_10_t st;
     const unsigned long long subseq = (unsigned long long)c.z | ((unsigned long long)c.w << 32);
     const unsigned long long block = (unsigned long long)c.x | ((unsigned long long)c.y << 32);
-    curand_init(seed, subseq, 4ull * block, &st);
+    curand_init(seed, subseq, 0ull, &st);
+    for (int k = 0; k < 4; ++k) skipahead(4ull * (block >> 2), &st);
+    skipahead(4ull * (block & 3ull), &st);
     out[i] = curand4(&st);
 }
 
