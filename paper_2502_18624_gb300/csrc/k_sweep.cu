@@ -21,9 +21,10 @@
 // unconditionally.  The classes come from a bit-sliced count of the four
 // disagreement words (two half adders: "exactly one disagreement" and
 // "none"), the same eq3/eq4 masks the paper builds with its compare-exchange
-// network.  Only uphill sites of a class whose threshold is neither 0 nor
-// 2^32 draw Philox; they are taken from a 64-bit mask of the chunk's active
-// sites with find-first-set, so a thread loops once per draw.
+// network.  Uphill sites of a class whose threshold is neither 0 nor 2^32
+// need a draw; the draw loop itself runs over every active site of the chunk
+// in a fixed order (see the comment there), two independent Philox chains per
+// iteration, and the per-site class is applied bit-parallel afterwards.
 //
 // Fused observables (colour-1 phase only): every bond has exactly one
 // colour-1 end, and a colour-1 site's four neighbours are colour 0 and
@@ -65,7 +66,7 @@ __device__ __forceinline__ void flush_count(long long* counter, long long v)
 }
 
 template <int CW, bool OBS>
-__global__ void __launch_bounds__(kSweepThreads) k_ising_phase(const __grid_constant__ IsingPhaseArgs a)
+__global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_constant__ IsingPhaseArgs a)
 {
     const uint32_t cpr = a.W / CW;  // chunks per row
     const uint64_t nitems = (uint64_t)a.L * cpr;
@@ -114,46 +115,69 @@ __global__ void __launch_bounds__(kSweepThreads) k_ising_phase(const __grid_cons
         const uint32_t p = (y + a.colour) & 1u;
         const uint64_t amask = kEven << p;
         uint64_t flip[CW], u8[CW], need[CW];
-        uint64_t dn[CW], ds[CW], dw[CW], de[CW];
+        int dpre = 0;  // disagreeing bonds of active sites after the flips decided without a draw
 #pragma unroll
         for (int k = 0; k < CW; ++k) {
-            dn[k] = c[k] ^ n[k];
-            ds[k] = c[k] ^ s[k];
-            dw[k] = c[k] ^ w[k];
-            de[k] = c[k] ^ e[k];
-            const uint64_t x1 = dn[k] ^ ds[k], a1 = dn[k] & ds[k];
-            const uint64_t x2 = dw[k] ^ de[k], a2 = dw[k] & de[k];
-            const uint64_t eq3 = (x1 ^ x2) & ~(a1 | a2);      // exactly one neighbour differs
-            const uint64_t eq4 = ~(dn[k] | ds[k] | dw[k] | de[k]);  // none differs
+            const uint64_t dn = c[k] ^ n[k], ds = c[k] ^ s[k], dw = c[k] ^ w[k], de = c[k] ^ e[k];
+            const uint64_t x1 = dn ^ ds, a1 = dn & ds;
+            const uint64_t x2 = dw ^ de, a2 = dw & de;
+            const uint64_t eq3 = (x1 ^ x2) & ~(a1 | a2);  // exactly one neighbour differs
+            const uint64_t eq4 = ~(dn | ds | dw | de);    // none differs
             u8[k] = eq4 & amask;
             const uint64_t u4 = eq3 & amask;
             flip[k] = (amask & ~(eq4 | eq3)) | (u8[k] & all8) | (u4 & all4);
             need[k] = (u8[k] & drw8) | (u4 & drw4);
+            if constexpr (OBS) {
+                const uint64_t f = flip[k];
+                dpre += __popcll((dn ^ f) & amask) + __popcll((ds ^ f) & amask) + __popcll((dw ^ f) & amask) +
+                        __popcll((de ^ f) & amask);
+            }
         }
 
-        // Active sites of both words interleaved into one mask: bit i is
-        // word (i & 1), bit position (i & ~1) | p.
-        uint64_t cm = need[0] >> p, c8 = u8[0] >> p;
-        if constexpr (CW == 2) {
-            cm |= (need[1] >> p) << 1;
-            c8 |= (u8[1] >> p) << 1;
-        }
-        accD += __popcll(cm);
-        if (cm) {
+        // Draws.  In SIMT a warp instruction costs its issue slot whatever its
+        // active mask, and across 32 chunks some lane almost always needs any
+        // given site position, so skipping individual sites saves nothing: every
+        // active site of the chunk draws, in a fixed order with no per-site
+        // bookkeeping, and is compared with both uphill thresholds.  The class
+        // and mode of each site are applied afterwards, 64 sites at a time.
+        accD += __popcll(need[0]) + (CW == 2 ? __popcll(need[CW - 1]) : 0);
+        if (__any_sync(kFull, (need[0] | need[CW - 1]) != 0)) {
             const uint64_t base = (uint64_t)y * a.L + (uint64_t)ch * (64u * CW);
-            const uint32_t base_lo = (uint32_t)base;  // chunks never straddle 2^32 (64*CW | 2^32)
+            const uint32_t site0 = (uint32_t)base + p;  // chunks never straddle 2^32 (64*CW | 2^32)
             const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, a.rk);
-            uint64_t acc = 0;
-            do {
-                const int i = __ffsll((long long)cm) - 1;
-                cm &= cm - 1;
-                const uint32_t off = ((uint32_t)(i & 1) << 6) | ((uint32_t)i & ~1u) | p;
-                const uint32_t u = philox_site_w0(base_lo + off, pc, a.rk);
-                const uint32_t th = ((c8 >> i) & 1) ? a.thr8 : a.thr4;
-                acc |= (uint64_t)(u < th) << i;
-            } while (cm);
-            flip[0] |= (acc & kEven) << p;
-            if constexpr (CW == 2) flip[1] |= ((acc >> 1) & kEven) << p;
+            uint32_t r4[CW][2], r8[CW][2];  // [word][32-bit half]: u < thr4, u < thr8
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t acc4[CW], acc8[CW];
+#pragma unroll
+                for (int k = 0; k < CW; ++k) acc4[k] = acc8[k] = 0;
+                uint32_t bit = 1u << p;
+#pragma unroll 2
+                for (uint32_t j = 0; j < 16; ++j) {
+                    const uint32_t off = 32u * half + 2u * j;
+#pragma unroll
+                    for (int k = 0; k < CW; ++k) {
+                        const uint32_t u = philox_site_w0(site0 + 64u * k + off, pc, a.rk);
+                        acc4[k] |= u < a.thr4 ? bit : 0u;
+                        acc8[k] |= u < a.thr8 ? bit : 0u;
+                    }
+                    bit <<= 2;
+                }
+#pragma unroll
+                for (int k = 0; k < CW; ++k) {
+                    r4[k][half] = acc4[k];
+                    r8[k][half] = acc8[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CW; ++k) {
+                const uint64_t R4 = ((uint64_t)r4[k][1] << 32) | r4[k][0];
+                const uint64_t R8 = ((uint64_t)r8[k][1] << 32) | r8[k][0];
+                const uint64_t acc8 = need[k] & u8[k] & R8, acc4 = need[k] & ~u8[k] & R4;
+                flip[k] |= acc8 | acc4;
+                // an accepted 3-agree site goes from 1 to 3 disagreeing bonds, a 4-agree site from 0 to 4
+                if constexpr (OBS) dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
+            }
         }
 
         uint64_t cn[CW];
@@ -166,15 +190,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_ising_phase(const __grid_cons
         }
 
         if constexpr (OBS) {
+            accB += 128 * CW - 2 * dpre;  // 32 active sites x 4 bonds per word
 #pragma unroll
-            for (int k = 0; k < CW; ++k) {
-                const uint64_t f = flip[k];
-                const int d = __popcll((dn[k] ^ f) & amask) + __popcll((ds[k] ^ f) & amask) +
-                              __popcll((dw[k] ^ f) & amask) + __popcll((de[k] ^ f) & amask);
-                accB += 128 - 2 * d;  // 32 active sites x 4 bonds
-                accM += 2 * __popcll(cn[k]) - 64;
-                accQ += 64;
-            }
+            for (int k = 0; k < CW; ++k) accM += 2 * __popcll(cn[k]) - 64;
+            accQ += 64 * CW;
         }
     }
     if constexpr (OBS) flush_obs(a.obs, accM, accB, accQ);
