@@ -36,12 +36,15 @@ if ROOT not in sys.path:
 METRIC = "spin flips/ns on 1 GB300 (Ising L=2^17) + % of roofline; batched vs plain flips/ns"
 UNIT = "flips/ns"
 TC = 2.0 / math.log(1.0 + math.sqrt(2.0))
-# Integer issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz (one
-# 32-bit integer instruction per lane per clock).
-SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-# Algorithmic integer work of one Philox4x32-10 block: 10 rounds x
-# (2 widening 32x32 multiplies + 2 three-input XORs).
+# The sweep is bound by integer multiplies (Philox4x32-10).  The integer
+# multiply-add pipe of an SM retires 64 32-bit IMAD lane-ops per clock (16
+# lanes on each of the 4 schedulers' FMA-heavy pipe), so the peak is
+# 152 SMs x 64 x 2070 MHz = 20.1 T IMAD-ops/s.
+SMS, IMAD_LANES_PER_SM, SM_MAX_MHZ = 152, 64, 2070.0
+ALU_PEAK_TOPS = SMS * IMAD_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+# Algorithmic multiply work of one Philox4x32-10 block by its definition:
+# 10 rounds x 2 widening 32x32->64 multiplies, each two 32-bit IMAD-ops
+# (high and low halves).
 OPS_PER_DRAW = 40
 
 WORKLOADS = {
@@ -252,12 +255,13 @@ def native(args, wl):
                 traffic = tr.get("bytes_per_launch")
         except Exception:
             traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "T IMAD-ops/s",
                 "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
                 "kernel": "k_ising_phase" if wl["model"] == 0 else "k_bc_phase",
                 "launch_ms": launch_s * 1e3, "draws_per_launch": draws_per_launch,
                 "ops_per_draw": OPS_PER_DRAW,
-                "peak_note": "integer issue peak 152 SM x 128 lanes x 2070 MHz (derived, not measured)",
+                "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "
+                             "achieved counts 40 IMAD-ops per needed Philox block",
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
     return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist)
 
