@@ -188,6 +188,35 @@ int lat_get_thresholds(lat_t* h, uint64_t* out, size_t n);
  * Synchronises the stream first.  NULL is accepted. */
 int lat_destroy(lat_t* h);
 
+/* Largest rmax accepted by lat_correlation_static. */
+#define LAT_STATIC_RMAX 4096u
+
+/* lat_correlation without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they measure, such as a library running inside another
+ * framework whose caching allocator owns the GPU's memory, or a serving loop
+ * in which cudaMalloc/cudaFree would synchronise the device.
+ *   model, L   as in lat_params (L a multiple of 64 within the same limits).
+ *   dev_spins  device pointer to a packed lattice in the layout of
+ *              lat_get_state (lat_create places it at the start of the
+ *              caller's dev_buf); read only.
+ *   rmax       0 <= rmax <= min(L/2, LAT_STATIC_RMAX); larger values give
+ *              LAT_EINVAL.
+ *   cx, cy     host arrays of rmax+1 entries, filled exactly as by
+ *              lat_correlation.
+ *   stream     cudaStream_t to run on (NULL = legacy default stream); the
+ *              call synchronises it before returning.
+ * Scratch: a fixed file-scope device array of 2*(LAT_STATIC_RMAX+1) int64
+ * (64 KiB) that every GPU loading the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array (it is cleared on
+ * the stream before each use), so calls whose work overlaps on the GPU race.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: LAT_EINVAL (bad arguments), LAT_ECUDA. */
+int lat_correlation_static(int32_t model, uint32_t L, const void* dev_spins, uint32_t rmax, int64_t* cx,
+                           int64_t* cy, void* stream);
+
 /* Static description of an error code. */
 const char* lat_strerror(int code);
 
