@@ -99,7 +99,9 @@ def test_multi_sweep_call_records_every_sweep(gpu, orc):
 
 
 @pytest.mark.parametrize("model", [0, 1])
-@pytest.mark.parametrize("L,rmax", [(64, 32), (64, 0), (128, 1), (192, 96), (256, 128), (512, 256), (320, 7)])
+@pytest.mark.parametrize("L,rmax", [(64, 32), (64, 0), (64, 31), (128, 1), (128, 33), (192, 96), (192, 63),
+                                    (256, 128), (256, 64), (320, 7), (320, 160), (512, 256), (512, 95),
+                                    (1024, 512), (1024, 100)])
 def test_correlation_parity(gpu, orc, model, L, rmax):
     T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
     lat = b.Lattice(model, L, T, 11, Delta=Delta)
