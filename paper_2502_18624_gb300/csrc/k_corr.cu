@@ -27,10 +27,8 @@ namespace latk {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kXWarpsMax = 4;     // rows in flight per x block (one per warp)
-constexpr uint32_t kXRows = 64;   // rows per warp in the x kernel
+constexpr int kXWarpsMax = 8;     // word-offset groups per x block (one per warp)
 constexpr int kYWarps = 8;        // distance groups per y block
-constexpr uint32_t kHY = 64;      // rows per y block
 
 template <int MODEL>
 struct Planes {
@@ -73,23 +71,25 @@ __device__ __forceinline__ uint32_t rot_word(const uint32_t* row, uint32_t W32, 
 
 template <int MODEL, int NQ>
 __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, uint32_t L, uint32_t rmax,
-                                                           long long* cx)
+                                                           uint32_t rows_per_block, long long* cx)
 {
+    // One row at a time is staged for the whole block; warp g of the block
+    // owns word offsets q0 = (blockIdx.y * nwarps + g) * NQ .. + NQ - 1.
     extern __shared__ uint32_t sm[];
     const uint32_t W = L / 64, W32 = L / 32;
     const int warp = threadIdx.x >> 5, s = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const uint32_t q0 = blockIdx.y * NQ;
-    uint32_t* row = sm + (size_t)warp * W32 * Planes<MODEL>::n;
+    const uint32_t q0 = (blockIdx.y * nwarps + warp) * NQ;
+    uint32_t* row = sm;
     int acc[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) acc[k] = 0;
-    const uint32_t ybeg = (blockIdx.x * nwarps + warp) * kXRows;
-    const uint32_t yend = min(ybeg + kXRows, L);
+    const uint32_t ybeg = blockIdx.x * rows_per_block;
+    const uint32_t yend = min(ybeg + rows_per_block, L);
     for (uint32_t y = ybeg; y < yend; ++y) {
-        __syncwarp();
-        load_row32<MODEL>(spins, W, y, row, s, 32);
-        __syncwarp();
+        __syncthreads();
+        load_row32<MODEL>(spins, W, y, row, threadIdx.x, blockDim.x);
+        __syncthreads();
         uint32_t win[NQ], wing[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
@@ -134,89 +134,124 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
     }
 }
 
+// y: a block owns a 32-word column strip, a segment of rows [y0, y0+H) and
+// the distances r0 .. r0 + kYWarps*NQ - 1.  The rows y0 + r0 + t (t >= 0)
+// that row y0 + y pairs with stream through a shared-memory ring of
+// YRing<NQ>::rows rows; each step stages NQ new A rows and NQ new ring rows,
+// so the register window's slot rotation restarts at every step and stays a
+// compile-time pattern.
+template <int NQ>
+struct YRing {
+    static constexpr uint32_t need = (kYWarps + 1) * NQ + 1;
+    static constexpr uint32_t rows = need <= 64 ? 64 : (need <= 128 ? 128 : 256);
+};
+
+template <int MODEL>
+__device__ __forceinline__ void load_strip_word(const void* spins, uint32_t W32, uint64_t y, uint32_t j, bool ok,
+                                                uint32_t& vn, uint32_t& vg)
+{
+    vn = 0;
+    vg = 0;
+    if (!ok) return;
+    if constexpr (MODEL == 0) {
+        vn = static_cast<const uint32_t*>(spins)[y * W32 + j];
+    } else {
+        const uint32_t* p = static_cast<const uint32_t*>(spins) + y * 2 * W32;
+        vn = p[4 * (j / 2) + (j & 1)];
+        vg = p[4 * (j / 2) + 2 + (j & 1)];
+    }
+}
+
 template <int MODEL, int NQ>
 __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint32_t L, uint32_t rmax,
-                                                        long long* cy)
+                                                        uint32_t rows_per_block, long long* cy)
 {
     extern __shared__ uint32_t sm[];
     constexpr int P = Planes<MODEL>::n;
-    constexpr uint32_t NB = kHY + kYWarps * NQ - 1;  // B rows per block
-    const uint32_t W = L / 64, W32 = L / 32;
+    constexpr uint32_t R = YRing<NQ>::rows;  // ring rows (power of two)
+    constexpr uint32_t D = kYWarps * NQ;     // distances per block
+    const uint32_t W32 = L / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t j0 = blockIdx.x * 32;             // first column word of the strip
-    const uint32_t tw = min(32u, W32 - j0);          // strip width in words
-    const uint32_t y0 = blockIdx.y * kHY;
-    const uint32_t r0 = blockIdx.z * (kYWarps * NQ);
-    uint32_t* A = sm;                      // kHY x 32 words per plane
-    uint32_t* B = sm + kHY * 32 * P;       // NB x 32 words per plane
+    const uint32_t j0 = blockIdx.x * 32;
+    const uint32_t tw = min(32u, W32 - j0);
+    const uint32_t y0 = blockIdx.y * rows_per_block;
+    const uint32_t H = min(rows_per_block, L - y0);
+    const uint32_t r0 = blockIdx.z * D;
+    uint32_t* ring = sm;                // R x 32 words per plane
+    uint32_t* arow = sm + R * 32 * P;   // NQ x 32 words per plane
 
-    // stage A rows y0.. and B rows y0 + r0 .. (mod L), plane-major per row block
-    for (uint32_t t = threadIdx.x; t < (kHY + NB) * 32; t += blockDim.x) {
+    // Lattice row of ring entry t is (y0 + r0 + t) mod L (staging only, so a
+    // plain modulo is cheap next to the pair work).
+    const uint32_t rb = (uint32_t)(((uint64_t)y0 + r0) % L);
+    auto brow = [L, rb](uint32_t t) { return (uint32_t)(((uint64_t)rb + t) % L); };
+    for (uint32_t t = threadIdx.x; t < D * 32; t += blockDim.x) {  // prefill ring entries 0 .. D-1
         const uint32_t rr = t / 32, c = t % 32;
-        const bool isA = rr < kHY;
-        const uint32_t rloc = isA ? rr : rr - kHY;
-        const uint64_t y = ((uint64_t)(isA ? y0 : y0 + r0) + rloc) % L;
-        uint32_t vn = 0, vg = 0;
-        if (c < tw) {
-            const uint32_t j = j0 + c;  // 32-bit column word
-            if constexpr (MODEL == 0) {
-                vn = static_cast<const uint32_t*>(spins)[y * W32 + j];
-            } else {
-                const uint32_t* p = static_cast<const uint32_t*>(spins) + y * 2 * W32;
-                vn = p[4 * (j / 2) + (j & 1)];
-                vg = p[4 * (j / 2) + 2 + (j & 1)];
-            }
-        }
-        uint32_t* base = isA ? A : B;
-        const uint32_t nrows = isA ? kHY : NB;
-        base[rloc * 32 + c] = vn;
-        if constexpr (MODEL == 1) base[nrows * 32 + rloc * 32 + c] = vg;
+        uint32_t vn, vg;
+        load_strip_word<MODEL>(spins, W32, brow(rr), j0 + c, c < tw, vn, vg);
+        ring[(rr % R) * 32 + c] = vn;
+        if constexpr (P == 2) ring[R * 32 + (rr % R) * 32 + c] = vg;
     }
-    __syncthreads();
 
-    const uint32_t g0 = (uint32_t)warp * NQ;  // this warp's first distance offset within the block
+    const uint32_t g0 = (uint32_t)warp * NQ;
     int acc[NQ];
     uint32_t win[NQ], wing[NQ];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-        acc[k] = 0;
-        win[k] = B[(g0 + k) * 32 + lane];
-        if constexpr (MODEL == 1) wing[k] = B[NB * 32 + (g0 + k) * 32 + lane];
-    }
-    for (uint32_t yb = 0; yb < kHY; yb += NQ) {
+    for (int k = 0; k < NQ; ++k) acc[k] = 0;
+    for (uint32_t ys = 0; ys < H; ys += NQ) {
+        __syncthreads();  // the previous step's ring rows and A rows are no longer read
+        for (uint32_t t = threadIdx.x; t < 2 * NQ * 32; t += blockDim.x) {
+            const uint32_t rr = (t / 32) % NQ, c = t % 32;
+            uint32_t vn, vg;
+            if (t < NQ * 32) {
+                const uint32_t ya = (uint32_t)(((uint64_t)y0 + ys + rr) % L);
+                load_strip_word<MODEL>(spins, W32, ya, j0 + c, c < tw && ys + rr < H, vn, vg);
+                arow[rr * 32 + c] = vn;
+                if constexpr (P == 2) arow[NQ * 32 + rr * 32 + c] = vg;
+            } else {
+                const uint32_t tb = D + ys + rr;
+                load_strip_word<MODEL>(spins, W32, brow(tb), j0 + c, c < tw, vn, vg);
+                ring[(tb % R) * 32 + c] = vn;
+                if constexpr (P == 2) ring[R * 32 + (tb % R) * 32 + c] = vg;
+            }
+        }
+        __syncthreads();
+        // window slot k holds ring entry ys + g0 + k at the start of the step
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const uint32_t tb = ys + g0 + k;
+            win[k] = ring[(tb % R) * 32 + lane];
+            if constexpr (P == 2) wing[k] = ring[R * 32 + (tb % R) * 32 + lane];
+        }
 #pragma unroll
         for (int u = 0; u < NQ; ++u) {
-            const uint32_t y = yb + u;
-            if (y < kHY) {
-                const uint32_t a = A[y * 32 + lane];
+            if (ys + u < H) {
+                const uint32_t a = arow[u * 32 + lane];
                 if constexpr (MODEL == 0) {
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) acc[k] += __popc(a ^ win[(u + k) % NQ]);
                 } else {
-                    const uint32_t ag = A[kHY * 32 + y * 32 + lane];
+                    const uint32_t ag = arow[NQ * 32 + u * 32 + lane];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
                         const uint32_t both = a & win[(u + k) % NQ];
                         acc[k] += __popc(both) - 2 * __popc(both & (ag ^ wing[(u + k) % NQ]));
                     }
                 }
-                const uint32_t nb = y + g0 + NQ;  // next B row for this slot (< NB except past the end)
-                if (nb < NB) {
-                    win[u] = B[nb * 32 + lane];
-                    if constexpr (MODEL == 1) wing[u] = B[NB * 32 + nb * 32 + lane];
-                }
+                const uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
+                win[u] = ring[(tb % R) * 32 + lane];
+                if constexpr (P == 2) wing[u] = ring[R * 32 + (tb % R) * 32 + lane];
             }
         }
     }
-    const bool valid = lane < tw;
+    const bool colok = (uint32_t)lane < tw;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
-        int v = valid ? acc[k] : 0;
+        int v = colok ? acc[k] : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
         const uint32_t r = r0 + g0 + k;
         if (lane == 0 && r <= rmax) {
-            const long long t = MODEL == 0 ? (long long)kHY * 32 * tw - 2ll * v : (long long)v;
+            const long long t = MODEL == 0 ? (long long)H * 32 * tw - 2ll * v : (long long)v;
             atomicAdd(reinterpret_cast<unsigned long long*>(cy + r), (unsigned long long)t);
         }
     }
@@ -242,52 +277,68 @@ int pick_nq(uint32_t count, uint32_t per_group_mult)
 }
 
 template <int MODEL, int NQ>
-cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx, cudaStream_t st)
+cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t per_warp = (size_t)W32 * Planes<MODEL>::n * sizeof(uint32_t);
-    int nwarps = (int)(160u * 1024u / per_warp);
-    nwarps = nwarps < 1 ? 1 : (nwarps > kXWarpsMax ? kXWarpsMax : nwarps);
-    const size_t smem = per_warp * nwarps;
+    const size_t smem = (size_t)W32 * Planes<MODEL>::n * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_corr_x<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint32_t qtot = rmax / 32 + 1;
-    const dim3 grid((L + nwarps * kXRows - 1) / (nwarps * kXRows), (qtot + NQ - 1) / NQ);
-    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, cx);
+    const uint32_t groups = (rmax / 32 + 1 + NQ - 1) / NQ;   // word-offset groups of NQ
+    const uint32_t nwarps = groups < (uint32_t)kXWarpsMax ? groups : (uint32_t)kXWarpsMax;
+    const uint32_t gy = (groups + nwarps - 1) / nwarps;
+    // rows per block: about 8 resident blocks per SM worth of work, at least 8 rows
+    const uint64_t want_blocks = (uint64_t)sms * 8 * 4 / gy + 1;
+    uint32_t rpb = (uint32_t)((L + want_blocks - 1) / want_blocks);
+    rpb = rpb < 8 ? 8 : rpb;
+    // per-lane popcount sums stay below 2^31: at most L per row
+    const uint32_t rmax_rows = (1u << 30) / L;
+    rpb = rpb > rmax_rows ? rmax_rows : rpb;
+    const dim3 grid((L + rpb - 1) / rpb, gy);
+    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, rpb, cx);
     return cudaGetLastError();
 }
 
 template <int MODEL, int NQ>
-cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy, cudaStream_t st)
+cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t smem = (size_t)(kHY + kHY + kYWarps * NQ - 1) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
+    const size_t smem = (size_t)(YRing<NQ>::rows + NQ) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_corr_y<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint32_t per_block = kYWarps * NQ;
-    const dim3 grid((W32 + 31) / 32, L / kHY, (rmax + per_block) / per_block);
-    k_corr_y<MODEL, NQ><<<grid, kYWarps * 32, smem, st>>>(spins, L, rmax, cy);
+    const uint32_t strips = (W32 + 31) / 32, chunks = (rmax + per_block) / per_block;
+    // row segments: enough blocks for about 4 per SM, segments of at least 4 steps
+    const uint64_t want = (uint64_t)sms * 4 / ((uint64_t)strips * chunks) + 1;
+    uint32_t rpb = (uint32_t)((L + want - 1) / want);
+    const uint32_t minrows = 4 * NQ;
+    rpb = rpb < minrows ? minrows : rpb;
+    rpb = (rpb + NQ - 1) / NQ * NQ;
+    const dim3 grid(strips, (L + rpb - 1) / rpb, chunks);
+    k_corr_y<MODEL, NQ><<<grid, kYWarps * 32, smem, st>>>(spins, L, rmax, rpb, cy);
     return cudaGetLastError();
 }
 
 template <int MODEL>
 cudaError_t launch_xy(const void* spins, uint32_t L, uint32_t rmax, long long* cx, long long* cy, cudaStream_t st)
 {
-    cudaError_t e;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     switch (pick_nq(rmax / 32 + 1, 1)) {
-        case 4: e = launch_x<MODEL, 4>(spins, L, rmax, cx, st); break;
-        case 8: e = launch_x<MODEL, 8>(spins, L, rmax, cx, st); break;
-        case 11: e = launch_x<MODEL, 11>(spins, L, rmax, cx, st); break;
-        case 13: e = launch_x<MODEL, 13>(spins, L, rmax, cx, st); break;
-        default: e = launch_x<MODEL, 16>(spins, L, rmax, cx, st); break;
+        case 4: e = launch_x<MODEL, 4>(spins, L, rmax, cx, sms, st); break;
+        case 8: e = launch_x<MODEL, 8>(spins, L, rmax, cx, sms, st); break;
+        case 11: e = launch_x<MODEL, 11>(spins, L, rmax, cx, sms, st); break;
+        case 13: e = launch_x<MODEL, 13>(spins, L, rmax, cx, sms, st); break;
+        default: e = launch_x<MODEL, 16>(spins, L, rmax, cx, sms, st); break;
     }
     if (e != cudaSuccess) return e;
     switch (pick_nq(rmax + 1, kYWarps)) {
-        case 4: return launch_y<MODEL, 4>(spins, L, rmax, cy, st);
-        case 8: return launch_y<MODEL, 8>(spins, L, rmax, cy, st);
-        case 11: return launch_y<MODEL, 11>(spins, L, rmax, cy, st);
-        case 13: return launch_y<MODEL, 13>(spins, L, rmax, cy, st);
-        default: return launch_y<MODEL, 16>(spins, L, rmax, cy, st);
+        case 4: return launch_y<MODEL, 4>(spins, L, rmax, cy, sms, st);
+        case 8: return launch_y<MODEL, 8>(spins, L, rmax, cy, sms, st);
+        case 11: return launch_y<MODEL, 11>(spins, L, rmax, cy, sms, st);
+        case 13: return launch_y<MODEL, 13>(spins, L, rmax, cy, sms, st);
+        default: return launch_y<MODEL, 16>(spins, L, rmax, cy, sms, st);
     }
 }
 
