@@ -188,6 +188,60 @@ int lat_get_thresholds(lat_t* h, uint64_t* out, size_t n);
  * Synchronises the stream first.  NULL is accepted. */
 int lat_destroy(lat_t* h);
 
+/* ---- Many lattices in one persistent launch ------------------------------
+ *
+ * A runner advances a set of lattices (handles from lat_create, of any mix
+ * of models, sizes and temperatures) by per-lattice sweep counts in one
+ * persistent kernel launch, replayed from a CUDA graph captured when the
+ * runner is created.  Every lattice ends bit-identical to the same sweeps
+ * run on it alone with lat_sweep (same counters, same per-site update), and
+ * its sweep index advances the same way.  The paper runs one lattice at a
+ * time (section 4); batching independent lattices is this library's own
+ * addition for many small systems.
+ *
+ * Inside the launch, phase k of a lattice waits for every tile of its phase
+ * k-1; each such wait is bounded (lat_runner_set_timeout), and a wait that
+ * gives up makes the run return LAT_ETIMEDOUT with the lattices in an
+ * unspecified state. */
+typedef struct lat_runner lat_runner_t;
+
+/* Device bytes a runner needs for up to max_lattices lattices and
+ * max_sweeps sweeps per lattice per run (0 if either is 0 or > 2^20). */
+size_t lat_runner_footprint(uint32_t max_lattices, uint32_t max_sweeps);
+
+/* Create a runner.  dev_buf/bytes/stream as in lat_create (NULL dev_buf
+ * lets the library allocate).  The runner also allocates a small pinned
+ * host staging area.  Errors: LAT_EINVAL, LAT_ENOMEM, LAT_ECUDA. */
+int lat_runner_create(uint32_t max_lattices, uint32_t max_sweeps, void* dev_buf, size_t bytes, void* stream,
+                      lat_runner_t** out);
+
+/* Schedule: items per tile for lattices of this model and L (a multiple of
+ * 256; 0 restores the default of 4096).  Results do not depend on it. */
+int lat_runner_set_tile(lat_runner_t* r, int32_t model, uint32_t L, uint32_t tile_items);
+
+/* Limit of one device-side wait, in nanoseconds (default 10 s). */
+int lat_runner_set_timeout(lat_runner_t* r, uint64_t ns);
+
+/* Failure-path testing: in later runs, every wait of lattices[index] (as
+ * passed to lat_runner_run) waits for a count that is never reached, so the
+ * run ends with LAT_ETIMEDOUT after the wait limit instead of hanging.
+ * index = 0xFFFFFFFF switches this off (the default). */
+int lat_runner_inject_stall(lat_runner_t* r, uint32_t index);
+
+/* Advance lattices[i] by nsweeps[i] sweeps (0 allowed), all in one launch
+ * on the runner's stream.  1 <= n <= max_lattices, nsweeps[i] <=
+ * max_sweeps, each handle at most once, Ising and Blume-Capel L <= 2^19.
+ * per_sweep may be NULL, or an array of n host pointers (each NULL or of
+ * nsweeps[i] records) that receive the exact (M, B, Q) and draw count after
+ * every sweep, as lat_sweep would.  The call first synchronises every
+ * handle's own stream, and synchronises the runner's stream before it
+ * returns.  Errors: LAT_EINVAL, LAT_ECUDA, LAT_ETIMEDOUT. */
+int lat_runner_run(lat_runner_t* r, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
+                   lat_obs* const* per_sweep);
+
+/* Release the runner (and its buffer, if the library allocated it). */
+int lat_runner_destroy(lat_runner_t* r);
+
 /* Largest rmax accepted by lat_correlation_static. */
 #define LAT_STATIC_RMAX 4096u
 

@@ -79,6 +79,13 @@ def load(build_if_missing: bool = True):
         "lat_get_thresholds": (i32, [P, P, sz]),
         "lat_destroy": (i32, [P]),
         "lat_strerror": (ctypes.c_char_p, [i32]),
+        "lat_runner_footprint": (sz, [u32, u32]),
+        "lat_runner_create": (i32, [u32, u32, P, sz, P, ctypes.POINTER(P)]),
+        "lat_runner_set_tile": (i32, [P, ctypes.c_int32, u32, u32]),
+        "lat_runner_set_timeout": (i32, [P, u64]),
+        "lat_runner_run": (i32, [P, P, u32, P, P]),
+        "lat_runner_destroy": (i32, [P]),
+        "lat_runner_inject_stall": (i32, [P, u32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -270,6 +277,95 @@ class Lattice:
     def close(self) -> None:
         if getattr(self, "handle", None):
             lat_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- runner: many lattices in one persistent launch -------------------------
+
+def lat_runner_footprint(max_lattices: int, max_sweeps: int) -> int:
+    return int(load().lat_runner_footprint(max_lattices, max_sweeps))
+
+
+def lat_runner_create(max_lattices: int, max_sweeps: int, dev_buf: int | None, nbytes: int,
+                      stream: int | None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lat_runner_create(max_lattices, max_sweeps, dev_buf, nbytes, stream, ctypes.byref(h)),
+           "lat_runner_create")
+    return h
+
+
+def lat_runner_set_tile(r, model: int, L: int, tile_items: int) -> None:
+    _check(load().lat_runner_set_tile(r, model, L, tile_items), "lat_runner_set_tile")
+
+
+def lat_runner_set_timeout(r, ns: int) -> None:
+    _check(load().lat_runner_set_timeout(r, ns), "lat_runner_set_timeout")
+
+
+def lat_runner_run(r, handles, nsweeps, record: bool = True):
+    """Advance handles[i] by nsweeps[i]; returns a list of per-sweep record arrays (or None)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    ns = np.ascontiguousarray(nsweeps, dtype=np.uint32)
+    outs = [np.zeros(int(k), dtype=OBS_DTYPE) for k in ns] if record else None
+    ptrs = (ctypes.c_void_p * n)(*[o.ctypes.data if (o is not None and o.size) else None for o in outs]) \
+        if record else None
+    code = load().lat_runner_run(r, hs, n, _ptr(ns), ptrs)
+    _check(code, "lat_runner_run")
+    return outs
+
+
+def lat_runner_inject_stall(r, index: int) -> None:
+    _check(load().lat_runner_inject_stall(r, index), "lat_runner_inject_stall")
+
+
+def lat_runner_destroy(r) -> None:
+    _check(load().lat_runner_destroy(r), "lat_runner_destroy")
+
+
+class Runner:
+    """A runner in a torch-owned device buffer, on the current stream."""
+
+    def __init__(self, max_lattices: int, max_sweeps: int, stream=None, device=None):
+        import torch
+
+        nbytes = lat_runner_footprint(max_lattices, max_sweeps)
+        if nbytes == 0:
+            raise LatError(LAT_EINVAL, "lat_runner_footprint")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.handle = lat_runner_create(max_lattices, max_sweeps, self.buffer.data_ptr(), nbytes,
+                                        self.stream.cuda_stream)
+        self.max_lattices, self.max_sweeps = max_lattices, max_sweeps
+
+    def set_tile(self, model: int, L: int, tile_items: int) -> None:
+        lat_runner_set_tile(self.handle, model, L, tile_items)
+
+    def set_timeout(self, ns: int) -> None:
+        lat_runner_set_timeout(self.handle, ns)
+
+    def inject_stall(self, index: int) -> None:
+        lat_runner_inject_stall(self.handle, index)
+
+    def run(self, lattices, nsweeps, record: bool = True):
+        return lat_runner_run(self.handle, [lt.handle for lt in lattices], nsweeps, record)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lat_runner_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/lat.h"
+#include "lat_handle.h"
 #include "lat_internal.cuh"
 
 using namespace latk;
@@ -43,10 +44,6 @@ size_t spins_bytes(const lat_params* p)
 {
     return (size_t)p->L * (p->L / 64) * sizeof(uint64_t) * (p->model == LAT_ISING ? 1 : 2);
 }
-
-struct Layout {
-    size_t spins, obs, corr, misc, stage, total, stage_bytes;
-};
 
 Layout layout_of(const lat_params* p)
 {
@@ -101,27 +98,6 @@ size_t build_table(const lat_params* p, uint64_t* t)
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
 
 }  // namespace
-
-struct lat {
-    lat_params p;
-    uint32_t W;
-    uint64_t thr[54];
-    size_t nthr;
-    Layout lay;
-    char* buf;
-    bool owns;
-    cudaStream_t stream;
-    uint64_t next_sweep;
-    LaunchShape ls;
-    RoundKeys rk;
-    std::vector<long long> host_obs;
-
-    void* spins() const { return buf + lay.spins; }
-    long long* obs() const { return reinterpret_cast<long long*>(buf + lay.obs); }
-    long long* corr() const { return reinterpret_cast<long long*>(buf + lay.corr); }
-    long long* misc() const { return reinterpret_cast<long long*>(buf + lay.misc); }
-    int8_t* stage() const { return reinterpret_cast<int8_t*>(buf + lay.stage); }
-};
 
 extern "C" {
 

@@ -1,0 +1,35 @@
+// lat_handle.h -- the private state behind a lat_t handle, shared by the
+// C ABI translation units (lat_api.cu, lat_multi.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/lat.h"
+#include "lat_internal.cuh"
+
+struct Layout {
+    size_t spins, obs, corr, misc, stage, total, stage_bytes;
+};
+
+struct lat {
+    lat_params p;
+    uint32_t W;
+    uint64_t thr[54];
+    size_t nthr;
+    Layout lay;
+    char* buf;
+    bool owns;
+    cudaStream_t stream;
+    uint64_t next_sweep;
+    latk::LaunchShape ls;
+    latk::RoundKeys rk;
+    std::vector<long long> host_obs;
+
+    void* spins() const { return buf + lay.spins; }
+    long long* obs() const { return reinterpret_cast<long long*>(buf + lay.obs); }
+    long long* corr() const { return reinterpret_cast<long long*>(buf + lay.corr); }
+    long long* misc() const { return reinterpret_cast<long long*>(buf + lay.misc); }
+    int8_t* stage() const { return reinterpret_cast<int8_t*>(buf + lay.stage); }
+};
+

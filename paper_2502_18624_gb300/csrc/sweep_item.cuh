@@ -1,0 +1,310 @@
+// sweep_item.cuh -- the update of one work item of a checkerboard colour
+// phase (section 3.1), shared by the one-lattice kernels (k_sweep.cu) and the
+// persistent multi-lattice kernel (k_multi.cu), so that both produce the same
+// bits from the same counters.
+//
+// Layout: row-major, W = L/64 words per row; bit b of word (y, j) is site
+// x = 64 j + b.  Colour-c sites of row y sit at bit positions b with
+// (b + y) % 2 == c.  An Ising item is a chunk of CW words (CW = 2: one 128-bit
+// access, 128 sites of which 64 are active; CW = 1 when L/64 is odd); a
+// Blume-Capel item is one (n, g) word pair (64 sites, 32 active).
+//
+// Consecutive lanes of a warp must hold consecutive items of the same phase,
+// and a warp's lanes must be all active or all inactive: the west/east edge
+// words are exchanged by warp shuffles.
+//
+// CG selects L2-coherent loads (ld.global.cg).  The one-lattice kernels
+// read a lattice that no other block of the same launch writes between
+// their kernel boundaries, so plain loads are safe; the persistent kernel
+// runs many phases in one launch, and a block may read a row it cached in
+// L1 during an earlier phase, so it bypasses L1.
+#pragma once
+#include "lat_internal.cuh"
+
+namespace latk {
+
+constexpr uint64_t kEvenBits = 0x5555555555555555ull;
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+
+template <bool CG, typename T>
+__device__ __forceinline__ T ld(const T* p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// Per-thread partial sums of one phase: (M, B, Q) of the fused reduction
+// and the number of Philox draws the phase needed.
+struct PhaseAcc {
+    long long M = 0, B = 0, Q = 0, D = 0;
+};
+
+__device__ __forceinline__ void flush_acc(long long* obs, long long* draws, PhaseAcc a)
+{
+    if (obs) {
+        const long long m = warp_sum(a.M), b = warp_sum(a.B), q = warp_sum(a.Q);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(obs + kObsM), (unsigned long long)m);
+            atomicAdd(reinterpret_cast<unsigned long long*>(obs + kObsB), (unsigned long long)b);
+            atomicAdd(reinterpret_cast<unsigned long long*>(obs + kObsQ), (unsigned long long)q);
+        }
+    }
+    if (draws) {
+        const long long d = warp_sum(a.D);
+        if ((threadIdx.x & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(draws), (unsigned long long)d);
+    }
+}
+
+// Parameters of one Ising colour phase.
+struct IsingPhase {
+    uint64_t* spins;
+    uint32_t L, W;
+    uint32_t sweep, colour;
+    uint32_t thr4, thr8;    // thresholds for s*h = 2 and s*h = 4
+    uint32_t mode4, mode8;  // ClassMode of the two uphill classes
+};
+
+// Ising decision (section 3.2): a site with all four neighbours equal to it
+// (dE = 8J) or exactly three (dE = 4J) is uphill; every other site flips
+// unconditionally.  The classes come from a bit-sliced count of the four
+// disagreement words (two half adders: "exactly one disagreement" and
+// "none"), the same eq3/eq4 masks the paper builds with its compare-exchange
+// network.  Uphill sites of a class whose threshold is neither 0 nor 2^32
+// need a draw.  In SIMT a warp instruction costs its issue slot whatever its
+// active mask, and across 32 chunks some lane almost always needs any given
+// site position, so skipping individual sites saves nothing: every active
+// site of the chunk draws, in a fixed order with no per-site bookkeeping
+// (two independent Philox chains per iteration), and is compared with both
+// uphill thresholds; the class and mode of each site are applied afterwards,
+// 64 sites at a time.
+//
+// Fused observables (colour-1 phase, OBS): every bond has exactly one
+// colour-1 end, and a colour-1 site's four neighbours are colour 0 and
+// already final, so B = sum over colour-1 sites of s * h after the update;
+// M and Q are summed over whole words, which are final after this phase.
+template <int CW, bool OBS, bool CG>
+__device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys& rk, uint64_t item, int lane,
+                                           PhaseAcc& acc)
+{
+    const uint32_t cpr = a.W / CW;  // chunks per row
+    const uint64_t all8 = a.mode8 == kAlwaysAccept ? ~0ull : 0ull;
+    const uint64_t all4 = a.mode4 == kAlwaysAccept ? ~0ull : 0ull;
+    const uint64_t drw8 = a.mode8 == kDraw ? ~0ull : 0ull;
+    const uint64_t drw4 = a.mode4 == kDraw ? ~0ull : 0ull;
+    const uint32_t y = (uint32_t)(item / cpr);
+    const uint32_t ch = (uint32_t)(item - (uint64_t)y * cpr);
+    const uint32_t yn = y == 0 ? a.L - 1 : y - 1;
+    const uint32_t ys = y + 1 == a.L ? 0 : y + 1;
+    uint64_t* row = a.spins + (uint64_t)y * a.W;
+    const uint64_t* rown = a.spins + (uint64_t)yn * a.W;
+    const uint64_t* rows = a.spins + (uint64_t)ys * a.W;
+
+    uint64_t c[CW], n[CW], s[CW];
+    if constexpr (CW == 2) {
+        const ulonglong2 vc = ld<CG>(reinterpret_cast<const ulonglong2*>(row) + ch);
+        const ulonglong2 vn = ld<CG>(reinterpret_cast<const ulonglong2*>(rown) + ch);
+        const ulonglong2 vs = ld<CG>(reinterpret_cast<const ulonglong2*>(rows) + ch);
+        c[0] = vc.x; c[1] = vc.y; n[0] = vn.x; n[1] = vn.y; s[0] = vs.x; s[1] = vs.y;
+    } else {
+        c[0] = ld<CG>(row + ch); n[0] = ld<CG>(rown + ch); s[0] = ld<CG>(rows + ch);
+    }
+    uint64_t left = __shfl_up_sync(kFullMask, c[CW - 1], 1);
+    uint64_t right = __shfl_down_sync(kFullMask, c[0], 1);
+    if (lane == 0 || ch == 0) left = ld<CG>(row + (ch == 0 ? a.W - 1 : ch * CW - 1));
+    if (lane == 31 || ch + 1 == cpr) right = ld<CG>(row + (ch + 1 == cpr ? 0 : (ch + 1) * CW));
+
+    uint64_t w[CW], e[CW];
+    if constexpr (CW == 2) {
+        w[0] = (c[0] << 1) | (left >> 63);
+        w[1] = (c[1] << 1) | (c[0] >> 63);
+        e[0] = (c[0] >> 1) | (c[1] << 63);
+        e[1] = (c[1] >> 1) | (right << 63);
+    } else {
+        w[0] = (c[0] << 1) | (left >> 63);
+        e[0] = (c[0] >> 1) | (right << 63);
+    }
+
+    const uint32_t p = (y + a.colour) & 1u;
+    const uint64_t amask = kEvenBits << p;
+    uint64_t flip[CW], u8[CW], need[CW];
+    int dpre = 0;  // disagreeing bonds of active sites after the flips decided without a draw
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+        const uint64_t dn = c[k] ^ n[k], ds = c[k] ^ s[k], dw = c[k] ^ w[k], de = c[k] ^ e[k];
+        const uint64_t x1 = dn ^ ds, a1 = dn & ds;
+        const uint64_t x2 = dw ^ de, a2 = dw & de;
+        const uint64_t eq3 = (x1 ^ x2) & ~(a1 | a2);  // exactly one neighbour differs
+        const uint64_t eq4 = ~(dn | ds | dw | de);    // none differs
+        u8[k] = eq4 & amask;
+        const uint64_t u4 = eq3 & amask;
+        flip[k] = (amask & ~(eq4 | eq3)) | (u8[k] & all8) | (u4 & all4);
+        need[k] = (u8[k] & drw8) | (u4 & drw4);
+        if constexpr (OBS) {
+            const uint64_t f = flip[k];
+            dpre += __popcll((dn ^ f) & amask) + __popcll((ds ^ f) & amask) + __popcll((dw ^ f) & amask) +
+                    __popcll((de ^ f) & amask);
+        }
+    }
+
+    acc.D += __popcll(need[0]) + (CW == 2 ? __popcll(need[CW - 1]) : 0);
+    if (__any_sync(kFullMask, (need[0] | need[CW - 1]) != 0)) {
+        const uint64_t base = (uint64_t)y * a.L + (uint64_t)ch * (64u * CW);
+        const uint32_t site0 = (uint32_t)base + p;  // chunks never straddle 2^32 (64*CW | 2^32)
+        const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
+        uint32_t r4[CW][2], r8[CW][2];  // [word][32-bit half]: u < thr4, u < thr8
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t acc4[CW], acc8[CW];
+#pragma unroll
+            for (int k = 0; k < CW; ++k) acc4[k] = acc8[k] = 0;
+            uint32_t bit = 1u << p;
+#pragma unroll 2
+            for (uint32_t j = 0; j < 16; ++j) {
+                const uint32_t off = 32u * half + 2u * j;
+#pragma unroll
+                for (int k = 0; k < CW; ++k) {
+                    const uint32_t u = philox_site_w0(site0 + 64u * k + off, pc, rk);
+                    acc4[k] |= u < a.thr4 ? bit : 0u;
+                    acc8[k] |= u < a.thr8 ? bit : 0u;
+                }
+                bit <<= 2;
+            }
+#pragma unroll
+            for (int k = 0; k < CW; ++k) {
+                r4[k][half] = acc4[k];
+                r8[k][half] = acc8[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CW; ++k) {
+            const uint64_t R4 = ((uint64_t)r4[k][1] << 32) | r4[k][0];
+            const uint64_t R8 = ((uint64_t)r8[k][1] << 32) | r8[k][0];
+            const uint64_t acc8 = need[k] & u8[k] & R8, acc4 = need[k] & ~u8[k] & R4;
+            flip[k] |= acc8 | acc4;
+            // an accepted 3-agree site goes from 1 to 3 disagreeing bonds, a 4-agree site from 0 to 4
+            if constexpr (OBS) dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
+        }
+    }
+
+    uint64_t cn[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) cn[k] = c[k] ^ flip[k];
+    if constexpr (CW == 2) {
+        reinterpret_cast<ulonglong2*>(row)[ch] = make_ulonglong2(cn[0], cn[1]);
+    } else {
+        row[ch] = cn[0];
+    }
+    if constexpr (OBS) {
+        acc.B += 128 * CW - 2 * dpre;  // 32 active sites x 4 bonds per word
+#pragma unroll
+        for (int k = 0; k < CW; ++k) acc.M += 2 * __popcll(cn[k]) - 64;
+        acc.Q += 64 * CW;
+    }
+}
+
+// Three-bit sum of four one-bit words (bit-sliced): returns b0 + 2 b1 + 4 b2.
+__device__ __forceinline__ void add4(uint64_t a, uint64_t b, uint64_t c, uint64_t d, uint64_t& b0, uint64_t& b1,
+                                     uint64_t& b2)
+{
+    const uint64_t s1 = a ^ b, c1 = a & b;
+    const uint64_t s2 = c ^ d, c2 = c & d;
+    b0 = s1 ^ s2;
+    const uint64_t c3 = s1 & s2;
+    b1 = c1 ^ c2 ^ c3;
+    b2 = (c1 & c2) | (c1 & c3) | (c2 & c3);
+}
+
+// New (n, g) code after accepting the proposal: index (s+1)*2 + b, two bits
+// (n | g << 1) per entry.  s=-1: {0, +1}; s=0: {-1, +1}; s=+1: {-1, 0}.
+constexpr uint32_t kBcNewCode = (0u << 0) | (1u << 2) | (3u << 4) | (1u << 6) | (3u << 8) | (0u << 10);
+
+struct BcPhase {
+    ulonglong2* spins;  // L rows of W (n, g) word pairs
+    uint32_t L, W;
+    uint32_t sweep, colour;
+};
+
+// Blume-Capel decision (Eq. (2)): every active site draws; the low bit of
+// word 1 picks the proposal among the two other values, and the move is
+// accepted iff the table entry for (s, proposal, h) is 2^32 or word 0 is
+// below it.  s_thr is the 54-entry table in shared memory.
+template <bool OBS, bool CG>
+__device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const unsigned long long* s_thr,
+                                        uint64_t item, int lane, PhaseAcc& acc)
+{
+    const uint32_t y = (uint32_t)(item / a.W);
+    const uint32_t j = (uint32_t)(item - (uint64_t)y * a.W);
+    const uint32_t yn = y == 0 ? a.L - 1 : y - 1;
+    const uint32_t ys = y + 1 == a.L ? 0 : y + 1;
+    ulonglong2* row = a.spins + (uint64_t)y * a.W;
+    const ulonglong2 c = ld<CG>(row + j);
+    const ulonglong2 vn = ld<CG>(a.spins + (uint64_t)yn * a.W + j);
+    const ulonglong2 vs = ld<CG>(a.spins + (uint64_t)ys * a.W + j);
+    ulonglong2 left, right;
+    left.x = __shfl_up_sync(kFullMask, c.x, 1);
+    left.y = __shfl_up_sync(kFullMask, c.y, 1);
+    right.x = __shfl_down_sync(kFullMask, c.x, 1);
+    right.y = __shfl_down_sync(kFullMask, c.y, 1);
+    if (lane == 0 || j == 0) left = ld<CG>(row + (j == 0 ? a.W - 1 : j - 1));
+    if (lane == 31 || j + 1 == a.W) right = ld<CG>(row + (j + 1 == a.W ? 0 : j + 1));
+
+    // Neighbour planes: n (nonzero) and g (negative).
+    const uint64_t nw = (c.x << 1) | (left.x >> 63), gw = (c.y << 1) | (left.y >> 63);
+    const uint64_t ne = (c.x >> 1) | (right.x << 63), ge = (c.y >> 1) | (right.y << 63);
+    uint64_t p0, p1, p2, q0, q1, q2;
+    add4(vn.x & ~vn.y, vs.x & ~vs.y, nw & ~gw, ne & ~ge, p0, p1, p2);  // +1 neighbours
+    add4(vn.x & vn.y, vs.x & vs.y, nw & gw, ne & ge, q0, q1, q2);      // -1 neighbours
+
+    const uint32_t p = (y + a.colour) & 1u;
+    const uint64_t base = (uint64_t)y * a.L + (uint64_t)j * 64u;
+    const uint32_t base_lo = (uint32_t)base;
+    const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
+    uint64_t nn = c.x, gg = c.y;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t b = 2u * k + p;
+        const uint32_t sn = (uint32_t)(c.x >> b) & 1u, sg = (uint32_t)(c.y >> b) & 1u;
+        const uint32_t sidx = sn ? (sg ? 0u : 2u) : 1u;  // s + 1
+        const uint32_t P = ((uint32_t)(p0 >> b) & 1u) | (((uint32_t)(p1 >> b) & 1u) << 1) |
+                           (((uint32_t)(p2 >> b) & 1u) << 2);
+        const uint32_t Nn = ((uint32_t)(q0 >> b) & 1u) | (((uint32_t)(q1 >> b) & 1u) << 1) |
+                            (((uint32_t)(q2 >> b) & 1u) << 2);
+        const uint32_t h4 = 4u + P - Nn;
+        const uint2 r = philox_site_w01(base_lo + b, pc, rk);
+        const uint32_t bp = r.y & 1u;
+        const uint32_t mv = sidx * 2u + bp;
+        if ((unsigned long long)r.x < s_thr[mv * 9u + h4]) {
+            const uint32_t code = (kBcNewCode >> (2u * mv)) & 3u;
+            const uint64_t bit = 1ull << b;
+            nn = (nn & ~bit) | ((uint64_t)(code & 1u) << b);
+            gg = (gg & ~bit) | ((uint64_t)(code >> 1) << b);
+        }
+    }
+    row[j] = make_ulonglong2(nn, gg);
+    acc.D += 32;
+
+    if constexpr (OBS) {
+        const uint64_t amask = kEvenBits << p;
+        const uint64_t na = nn & amask;
+        const uint64_t nbn[4] = {vn.x, vs.x, nw, ne}, nbg[4] = {vn.y, vs.y, gw, ge};
+        long long bsum = 0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const uint64_t both = na & nbn[d];
+            bsum += __popcll(both) - 2 * __popcll(both & (gg ^ nbg[d]));
+        }
+        acc.B += bsum;
+        acc.M += __popcll(nn & ~gg) - __popcll(nn & gg);
+        acc.Q += __popcll(nn);
+    }
+}
+
+}  // namespace latk
