@@ -240,6 +240,7 @@ def native(args, wl):
     if not args.no_e2e:
         e2e = end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash)
     line_e2e = e2e
+    batched = None if args.no_batched else batched_leg(b, stream, device, dist, world)
 
     # roofline of the dominant kernel (the colour-phase sweep kernel)
     launch_s = (sweep_ms / 1e3) / nlaunch
@@ -263,7 +264,60 @@ def native(args, wl):
                 "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "
                              "achieved counts 40 IMAD-ops per needed Philox block",
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
-    return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist)
+    return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist,
+                  batched)
+
+
+def batched_leg(b, stream, device, dist, world):
+    """The 512-replica mixed workload: one runner launch against the plain path.
+
+    Both legs start from the replicas' quenches and run 500 sweeps with the
+    exact (M, B, Q) after every sweep; the plain leg runs lat_sweep on one
+    replica after another.  Every replica must end bit-identical in both."""
+    import torch
+
+    from paper_2502_18624_gb300 import autotune, workloads
+    jobs = workloads.batched_replicas()
+    sweeps = jobs[0].sweeps
+    sched = autotune.tune(jobs, use_cache=False)
+    mk = lambda: [b.Lattice(j.model, j.L, j.T, j.seed, Delta=j.Delta, stream=stream, device=device) for j in jobs]
+    updates = float(sum(j.L * j.L for j in jobs)) * sweeps
+
+    runner = b.Runner(len(jobs), sweeps, stream=stream, device=device)
+    autotune.apply(runner, sched)
+    lats = mk()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    runner.run(lats, [sweeps] * len(jobs))
+    e1.record(stream)
+    e1.synchronize()
+    t_batched = reduce_max(dist, e0.elapsed_time(e1) / 1e3, device)
+    hb = [lt.hash() for lt in lats]
+    for lt in lats:
+        lt.close()
+    runner.close()
+
+    lats = mk()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    e0.record(stream)
+    for lt in lats:
+        lt.sweep(sweeps)
+    e1.record(stream)
+    e1.synchronize()
+    t_plain = reduce_max(dist, e0.elapsed_time(e1) / 1e3, device)
+    hp = [lt.hash() for lt in lats]
+    for lt in lats:
+        lt.close()
+    assert hb == hp, "batched run differs from the plain path"
+    return {"value": whole_job(updates, world, t_batched), "plain": whole_job(updates, world, t_plain),
+            "unit": UNIT, "speedup": t_plain / t_batched, "replicas": len(jobs), "sweeps": sweeps,
+            "spins": int(sum(j.L * j.L for j in jobs)), "bit_exact": True,
+            "tiles": {"%s L=%d" % ("ising" if m == 0 else "bc", L): t for (m, L), t in sorted(sched.items())},
+            "workload": "512 replicas, L in {64..4096} with weights 1/L, 384 Ising T~U[0.8,1.2]Tc, "
+                        "128 Blume-Capel Delta=1 T~U[1.2,1.6], seeds 2025+id, 500 sweeps, E/M every sweep"}
 
 
 def end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash):
@@ -290,7 +344,7 @@ def end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash):
             "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
 
 
-def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, e2e, clocks, dist):
+def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, e2e, clocks, dist, batched=None):
     L2 = float(wl["L"]) ** 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": max_secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
@@ -301,6 +355,8 @@ def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, rooflin
                        "l2": "inputs larger than L2 (packed lattice %d MiB vs 126 MiB L2), no flush" %
                              (L2 / 8 / (1 << 20) * (1 if wl["model"] == 0 else 2))},
             "roofline": roofline, "e2e": e2e, "gpu_launches": nlaunch + 2 * ncorr, "clocks": clocks}
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0:
         if args.cpu_seconds > 0:
             line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
@@ -401,6 +457,7 @@ def main(argv=None):
                     help="oracle CPU-baseline budget; 0 skips it (profiling runs)")
     ap.add_argument("--L", type=int, default=None, help="override the linear size (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain leg (profiling runs)")
     args = ap.parse_args(argv)
     wl = dict(WORKLOADS[args.workload])
     if args.L:
