@@ -410,6 +410,65 @@ def cpu_baseline(wl, budget_s: float = 12.0):
                       (n, wl["L"], el)}
 
 
+def served_bench(args):
+    """Continuous batching on a bounded prefix of the served job stream,
+    against the same jobs run one after another on the plain path."""
+    import torch
+
+    from paper_2502_18624_gb300 import autotune, serve, workloads
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    jobs = workloads.served_jobs(rate=args.rate)[: args.jobs]
+    if world > 1:
+        jobs = [workloads.Job(j.id, j.model, j.L, j.T, j.Delta, j.seed + 1000003 * rank, j.sweeps, j.arrival)
+                for j in jobs]
+    sample = workloads.served_jobs(n=64, rate=args.rate, seed=777)
+    tiles = autotune.tune(sample, use_cache=False)
+    # warm-up: a few tiny jobs through both paths
+    warm = workloads.served_jobs(n=6, rate=1e6, seed=5, kmin=8, kmax=8, smin=4, smax=8)
+    for _ in range(max(1, args.warmup // 3)):
+        e = serve.GpuEngine(8, 8)
+        serve.Server(e, 1 << 30, 8).run(warm)
+        e.close()
+    eng = serve.GpuEngine(args.max_batch, args.step_sweeps, tiles=tiles)
+    srv = serve.Server(eng, mem_budget=int(args.mem_gib * (1 << 30)), max_batch=args.max_batch,
+                       step_updates=args.step_updates, max_step_sweeps=args.step_sweeps)
+    sampler = ClockSampler(gpu_id_for(local)).start()
+    barrier(dist, device)
+    res = srv.run(jobs)
+    clocks = sampler.stop()
+    eng.close()
+    s_srv = serve.summarize(res, srv.wall)
+    seq_eng = serve.GpuEngine(1, 1)
+    barrier(dist, device)
+    t0 = time.perf_counter()
+    seq = serve.run_sequential(seq_eng, jobs)
+    seq_wall = time.perf_counter() - t0
+    seq_eng.close()
+    s_seq = serve.summarize(seq, seq_wall)
+    exact = all(serve.same_results(a, b) for a, b in zip(res, seq))
+    wall = reduce_max(dist, srv.wall, device)
+    value = whole_job(s_srv["updates"], world, wall)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(jobs),
+                "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "served: first %d jobs of the Poisson stream (%.0f jobs/s, Ising p=0.7 / "
+                                       "Blume-Capel Delta in {0.5,1,1.5}, L=2^8..2^14, T=[0.7,1.3] Tc_ref, "
+                                       "sweeps log-uniform 10..10000, C(r<=min(L/2,1024)) at sweeps 2^k), "
+                                       "seed 20250" % (len(jobs), args.rate),
+                           "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch,
+                           "step_updates": args.step_updates, "parallelism": "replicas" if world > 1 else "single"},
+                "served": dict(s_srv, steps=srv.steps, peak_batch=srv.peak_batch, peak_mem=srv.peak_mem),
+                "sequential_plain": s_seq, "bit_exact": exact, "clocks": clocks,
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -452,13 +511,24 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ising-tc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="ising-tc")
+    ap.add_argument("--jobs", type=int, default=200, help="served: jobs taken from the start of the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: mean arrival rate, jobs/s")
+    ap.add_argument("--mem-gib", type=float, default=48.0, help="served: device memory budget")
+    ap.add_argument("--max-batch", type=int, default=256, help="served: most jobs resident at once")
+    ap.add_argument("--step-updates", type=float, default=1e10, help="served: work per step (spin updates)")
+    ap.add_argument("--step-sweeps", type=int, default=256, help="served: most sweeps per job per step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="oracle CPU-baseline budget; 0 skips it (profiling runs)")
     ap.add_argument("--L", type=int, default=None, help="override the linear size (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain leg (profiling runs)")
     args = ap.parse_args(argv)
+    if args.workload == "served":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the served workload has no CPU reference arm"}))
+            return
+        return served_bench(args)
     wl = dict(WORKLOADS[args.workload])
     if args.L:
         wl["L"] = args.L

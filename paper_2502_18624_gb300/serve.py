@@ -1,0 +1,212 @@
+"""Served simulation jobs with continuous batching.
+
+Jobs (workloads.Job: model, L, T, Delta, seed, sweeps, arrival time) arrive
+as a stream.  The server loop works in steps.  At every step boundary it
+admits arrived jobs first-come-first-served while their device footprint
+fits the memory budget (a job's lattice and per-job workspace stay resident
+on the device until the job ends), then advances every resident job in one
+runner launch (many lattices, one persistent kernel), each by as many
+sweeps as fit the step's work budget without passing its next measurement
+point.  Measurements follow section 3.3's log-spaced times in the form this
+library uses: after 1, 2, 4, 8, ... completed sweeps a job's C(r) is taken
+along both axes for r <= min(L/2, rmax_cap).  The exact (M, B, Q) of every
+sweep are recorded.  A finished job releases its memory at once, so jobs
+that arrived meanwhile are admitted at the next step and their work
+overlaps with the jobs already on the device.
+
+Every job's results equal those of the same job run alone on the plain
+path (run_sequential), because the runner reproduces lat_sweep bit for bit.
+The engine is a parameter so that the scheduling logic can be tested on the
+CPU with a fake engine.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class JobResult:
+    job: object
+    admitted: float = -1.0
+    completed: float = -1.0
+    obs: list = field(default_factory=list)      # per-sweep record arrays, in order
+    corr: dict = field(default_factory=dict)     # completed sweeps -> (cx, cy)
+    final_hash: int = 0
+
+    @property
+    def latency(self) -> float:
+        return self.completed - self.job.arrival
+
+
+def next_measurement(done: int) -> int:
+    """The next power of two strictly above `done` (measurement after 1, 2, 4, ... sweeps)."""
+    p = 1
+    while p <= done:
+        p *= 2
+    return p
+
+
+def plan_step(active, budget_updates: float, max_sweeps: int):
+    """Sweeps per resident job for one step.
+
+    active: list of (L, sweeps_done, sweeps_total).  Every job gets the same
+    quota q = budget / sum(L^2) (at least 1), capped by max_sweeps, by its
+    remaining sweeps and by its next measurement point."""
+    if not active:
+        return []
+    tot = float(sum(L * L for (L, _, _) in active))
+    q = int(max(1, min(max_sweeps, budget_updates // max(tot, 1.0))))
+    out = []
+    for (L, done, total) in active:
+        k = min(q, total - done, next_measurement(done) - done)
+        out.append(max(0, k))
+    return out
+
+
+class GpuEngine:
+    """The device side: lattices in torch-owned buffers, one runner."""
+
+    def __init__(self, max_jobs: int, max_step_sweeps: int, rmax_cap: int = 1024, tiles=None):
+        from . import binding as b
+        self.b = b
+        self.runner = b.Runner(max_jobs, max_step_sweeps)
+        if tiles:
+            for (m, L), t in tiles.items():
+                self.runner.set_tile(m, L, t)
+        self.rmax_cap = rmax_cap
+
+    def footprint(self, job) -> int:
+        return self.b.lat_footprint(self.b.make_params(job.model, job.L, job.T, job.seed, Delta=job.Delta))
+
+    def create(self, job):
+        return self.b.Lattice(job.model, job.L, job.T, job.seed, Delta=job.Delta, stream=self.runner.stream)
+
+    def advance(self, handles, nsweeps):
+        return self.runner.run(handles, nsweeps)
+
+    def measure(self, h):
+        return h.correlation(min(h.L // 2, self.rmax_cap))
+
+    def finish(self, h) -> int:
+        v = h.hash()
+        h.close()
+        return v
+
+    def close(self):
+        self.runner.close()
+
+
+class Server:
+    def __init__(self, engine, mem_budget: int, max_batch: int, step_updates: float = 2e9,
+                 max_step_sweeps: int = 256, clock=time.perf_counter, sleep=time.sleep):
+        self.engine = engine
+        self.mem_budget = mem_budget
+        self.max_batch = max_batch
+        self.step_updates = step_updates
+        self.max_step_sweeps = max_step_sweeps
+        self.clock, self.sleep = clock, sleep
+        self.steps = 0
+        self.peak_mem = 0
+        self.peak_batch = 0
+
+    def run(self, jobs):
+        jobs = sorted(jobs, key=lambda j: (j.arrival, j.id))
+        arrivals = deque(jobs)
+        pending = deque()
+        active = []  # [result, handle, done, footprint]
+        results = {}
+        used = 0
+        t0 = self.clock()
+        while arrivals or pending or active:
+            now = self.clock() - t0
+            while arrivals and arrivals[0].arrival <= now:
+                j = arrivals.popleft()
+                results[j.id] = JobResult(j)
+                pending.append(j)
+            # admission: first come, first served, by device footprint
+            while pending and len(active) < self.max_batch:
+                j = pending[0]
+                fp = self.engine.footprint(j)
+                if fp > self.mem_budget:
+                    raise ValueError("job %d needs %d bytes, more than the whole budget" % (j.id, fp))
+                if used + fp > self.mem_budget:
+                    break
+                pending.popleft()
+                used += fp
+                self.peak_mem = max(self.peak_mem, used)
+                r = results[j.id]
+                r.admitted = self.clock() - t0
+                active.append([r, self.engine.create(j), 0, fp])
+            if not active:
+                if arrivals:
+                    self.sleep(max(0.0, arrivals[0].arrival - (self.clock() - t0)))
+                continue
+            self.peak_batch = max(self.peak_batch, len(active))
+            plan = plan_step([(a[0].job.L, a[2], a[0].job.sweeps) for a in active], self.step_updates,
+                             self.max_step_sweeps)
+            obs = self.engine.advance([a[1] for a in active], plan)
+            self.steps += 1
+            keep = []
+            for a, k, o in zip(active, plan, obs):
+                r, h = a[0], a[1]
+                if k:
+                    r.obs.append(o)
+                    a[2] += k
+                if a[2] > 0 and (a[2] & (a[2] - 1)) == 0 and a[2] not in r.corr:
+                    r.corr[a[2]] = self.engine.measure(h)
+                if a[2] >= r.job.sweeps:
+                    r.final_hash = self.engine.finish(h)
+                    r.completed = self.clock() - t0
+                    used -= a[3]
+                else:
+                    keep.append(a)
+            active = keep
+        self.wall = self.clock() - t0
+        return [results[j.id] for j in jobs]
+
+
+def run_sequential(engine, jobs, clock=time.perf_counter, sleep=time.sleep):
+    """The plain baseline: jobs one at a time in arrival order, each alone on
+    the one-lattice path (lat_sweep up to each measurement point)."""
+    jobs = sorted(jobs, key=lambda j: (j.arrival, j.id))
+    out = []
+    t0 = clock()
+    for j in jobs:
+        now = clock() - t0
+        if now < j.arrival:
+            sleep(j.arrival - now)
+        r = JobResult(j, admitted=clock() - t0)
+        h = engine.create(j)
+        done = 0
+        while done < j.sweeps:
+            k = min(j.sweeps, next_measurement(done)) - done
+            r.obs.append(h.sweep(k))
+            done += k
+            if (done & (done - 1)) == 0:
+                r.corr[done] = engine.measure(h)
+        r.final_hash = engine.finish(h)
+        r.completed = clock() - t0
+        out.append(r)
+    return out
+
+
+def summarize(results, wall: float) -> dict:
+    lat = np.array([r.latency for r in results])
+    updates = float(sum(r.job.L * r.job.L * r.job.sweeps for r in results))
+    return {"jobs": len(results), "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "wall_s": wall,
+            "updates": updates, "flips_per_ns": updates / wall / 1e9}
+
+
+def same_results(a: JobResult, b: JobResult) -> bool:
+    """Bit-exact comparison of two runs of one job."""
+    oa = np.concatenate(a.obs) if a.obs else np.zeros(0)
+    ob = np.concatenate(b.obs) if b.obs else np.zeros(0)
+    if a.final_hash != b.final_hash or not np.array_equal(oa, ob) or a.corr.keys() != b.corr.keys():
+        return False
+    return all(np.array_equal(a.corr[t][0], b.corr[t][0]) and np.array_equal(a.corr[t][1], b.corr[t][1])
+               for t in a.corr)

@@ -1,0 +1,134 @@
+"""Host-side logic of the served loop, on the CPU with a fake engine and a
+virtual clock: admission by footprint (first come, first served, never over
+budget), continuous batching (jobs that arrive while others run are admitted
+at the next step), measurement points at 1, 2, 4, ... sweeps, and step
+plans that never pass a measurement point or a job's end."""
+import numpy as np
+import pytest
+
+from paper_2502_18624_gb300 import serve, workloads
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 0.0)
+
+
+class FakeHandle:
+    def __init__(self, job):
+        self.job, self.L, self.done, self.closed = job, job.L, 0, False
+
+
+class FakeEngine:
+    """Records everything the server asks for; time advances with the work."""
+
+    def __init__(self, clock, rate_updates_per_s=1e11):
+        self.clock, self.rate = clock, rate_updates_per_s
+        self.live, self.peak_live, self.events = 0, 0, []
+
+    def footprint(self, job):
+        return workloads.footprint_bytes(job) + 4096
+
+    def create(self, job):
+        self.live += self.footprint(job)
+        self.peak_live = max(self.peak_live, self.live)
+        self.events.append(("create", job.id, self.clock()))
+        return FakeHandle(job)
+
+    def advance(self, handles, nsweeps):
+        assert len(set(map(id, handles))) == len(handles)
+        work = 0.0
+        out = []
+        for h, k in zip(handles, nsweeps):
+            assert not h.closed and 0 <= k and h.done + k <= h.job.sweeps
+            rec = np.zeros(k, dtype=[("sweep", np.uint64)])
+            rec["sweep"] = np.arange(h.done + 1, h.done + k + 1)
+            h.done += k
+            work += h.L * h.L * k
+            out.append(rec)
+        self.clock.t += work / self.rate + 1e-4
+        return out
+
+    def measure(self, h):
+        self.events.append(("measure", h.job.id, h.done))
+        return (np.array([h.done]), np.array([h.done]))
+
+    def finish(self, h):
+        assert h.done == h.job.sweeps
+        h.closed = True
+        self.live -= self.footprint(h.job)
+        return h.job.id * 7 + h.done
+
+
+def _jobs(n=60, seed=5):
+    return workloads.served_jobs(n=n, rate=50.0, seed=seed, kmin=6, kmax=10, smin=3, smax=300)
+
+
+def test_all_jobs_finish_with_every_sweep_and_measurement():
+    clock = Clock()
+    eng = FakeEngine(clock)
+    srv = serve.Server(eng, mem_budget=600_000, max_batch=16, step_updates=5e6, max_step_sweeps=64,
+                       clock=clock, sleep=clock.sleep)
+    jobs = _jobs()
+    res = srv.run(jobs)
+    for r in res:
+        sweeps = np.concatenate(r.obs)["sweep"]
+        assert list(sweeps) == list(range(1, r.job.sweeps + 1))
+        expect = [2 ** k for k in range(0, 20) if 2 ** k <= r.job.sweeps]
+        assert sorted(r.corr) == expect
+        assert r.final_hash == r.job.id * 7 + r.job.sweeps
+        assert r.completed >= r.admitted >= r.job.arrival - 1e-12
+    assert eng.live == 0
+
+
+def test_memory_budget_is_never_exceeded_and_admission_is_fifo():
+    clock = Clock()
+    eng = FakeEngine(clock)
+    budget = 400_000
+    srv = serve.Server(eng, mem_budget=budget, max_batch=64, step_updates=5e6, max_step_sweeps=64,
+                       clock=clock, sleep=clock.sleep)
+    jobs = _jobs(80, 9)
+    srv.run(jobs)
+    assert eng.peak_live <= budget
+    created = [e[1] for e in eng.events if e[0] == "create"]
+    assert created == [j.id for j in sorted(jobs, key=lambda j: (j.arrival, j.id))]
+
+
+def test_jobs_arriving_during_work_join_running_batches():
+    clock = Clock()
+    eng = FakeEngine(clock, rate_updates_per_s=2e9)
+    srv = serve.Server(eng, mem_budget=10**9, max_batch=64, step_updates=2e6, max_step_sweeps=32,
+                       clock=clock, sleep=clock.sleep)
+    res = srv.run(_jobs(40, 3))
+    # some job was admitted while another, admitted earlier, was still running
+    overlap = any(b.admitted < a.completed and b.admitted > a.admitted for a in res for b in res)
+    assert overlap and srv.peak_batch > 1
+
+
+def test_oversized_job_is_rejected():
+    clock = Clock()
+    srv = serve.Server(FakeEngine(clock), mem_budget=1000, max_batch=4, clock=clock, sleep=clock.sleep)
+    with pytest.raises(ValueError):
+        srv.run([workloads.Job(0, 0, 4096, 2.0, 0.0, 1, 5, 0.0)])
+
+
+@pytest.mark.parametrize("done,total,expect_cap", [(0, 10, 1), (1, 10, 1), (2, 10, 2), (5, 100, 3), (64, 70, 6)])
+def test_plan_step_respects_measurements_and_ends(done, total, expect_cap):
+    k = serve.plan_step([(64, done, total)], budget_updates=1e12, max_sweeps=1000)[0]
+    assert k == expect_cap
+    assert serve.next_measurement(done) - done >= k and total - done >= k
+
+
+def test_plan_step_shares_the_budget():
+    ks = serve.plan_step([(1024, 0, 10**6 - 1), (2048, 3, 10**6 - 1)], budget_updates=1024**2 * 5 * 10, max_sweeps=64)
+    # quota = budget / (1024^2 + 2048^2) = 10, capped by the next measurement points (1 and 1)
+    assert ks == [1, 1]
+    ks = serve.plan_step([(1024, 64, 10**6 - 1), (2048, 64, 10**6 - 1)], budget_updates=1024**2 * 5 * 10,
+                         max_sweeps=64)
+    assert ks == [10, 10]
