@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_c
 }
 
 template <bool OBS>
-__global__ void __launch_bounds__(kSweepThreads) k_bc_phase(const __grid_constant__ BcPhaseArgs a)
+__global__ void __launch_bounds__(kSweepThreads, 3) k_bc_phase(const __grid_constant__ BcPhaseArgs a)
 {
     __shared__ unsigned long long s_thr[54];
     for (int i = threadIdx.x; i < 54; i += blockDim.x) s_thr[i] = a.thr[i];

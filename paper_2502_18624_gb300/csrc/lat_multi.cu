@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -103,7 +104,8 @@ __device__ __forceinline__ void bc_tile(const MultiDesc& d, const unsigned long 
     for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x) bc_item<OBS, true>(ph, rk, s_thr, it, lane, acc);
 }
 
-__global__ void __launch_bounds__(kMultiThreads, 2)
+template <int MINB>
+__global__ void __launch_bounds__(kMultiThreads, MINB)
     k_multi(const MultiDesc* __restrict__ desc, const uint32_t* __restrict__ tile_prefix,
             const unsigned long long* __restrict__ phase_base, const uint32_t* __restrict__ active,
             unsigned int* done, MultiCtl* ctl)
@@ -225,6 +227,7 @@ struct lat_runner {
     bool owns;
     cudaStream_t stream;
     int grid;
+    int minb;  // resident blocks per SM the persistent kernel is built for (2 or 3)
     unsigned long long timeout_ns;
     uint32_t stall;  // input index whose waits never complete (failure-path tests), or ~0
     std::map<std::pair<int, uint32_t>, uint32_t> tile_of;  // (model, L) -> items per tile
@@ -259,8 +262,12 @@ cudaError_t enqueue_run(lat_runner* R, cudaStream_t st, uint32_t n)
     cudaError_t e = cudaMemsetAsync(R->d_done(), 0, (size_t)R->cap * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     (void)n;
-    k_multi<<<R->grid, kMultiThreads, 0, st>>>(R->d_desc(), R->d_tile_prefix(), R->d_phase_base(), R->d_active(),
-                                               R->d_done(), R->d_ctl());
+    if (R->minb == 3)
+        k_multi<3><<<R->grid, kMultiThreads, 0, st>>>(R->d_desc(), R->d_tile_prefix(), R->d_phase_base(),
+                                                      R->d_active(), R->d_done(), R->d_ctl());
+    else
+        k_multi<2><<<R->grid, kMultiThreads, 0, st>>>(R->d_desc(), R->d_tile_prefix(), R->d_phase_base(),
+                                                      R->d_active(), R->d_done(), R->d_ctl());
     return cudaGetLastError();
 }
 
@@ -283,7 +290,15 @@ int lat_runner_create(uint32_t max_lattices, uint32_t max_sweeps, void* dev_buf,
     int dev = 0, sms = 0, bpsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LAT_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAT_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_multi, kMultiThreads, 0) != cudaSuccess) return LAT_ECUDA;
+    // Two resident blocks per SM give the kernel the registers it needs
+    // without spilling, which measured faster than three blocks with spills
+    // on the mixed 512-lattice workload; LAT_MULTI_BLOCKS=3 selects the other.
+    const char* env = std::getenv("LAT_MULTI_BLOCKS");
+    const int minb = (env && env[0] == '3') ? 3 : 2;
+    const cudaError_t oe = minb == 3
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_multi<3>, kMultiThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_multi<2>, kMultiThreads, 0);
+    if (oe != cudaSuccess) return LAT_ECUDA;
     lat_runner* R = new (std::nothrow) lat_runner();
     if (!R) return LAT_ENOMEM;
     R->cap = max_lattices;
@@ -291,6 +306,7 @@ int lat_runner_create(uint32_t max_lattices, uint32_t max_sweeps, void* dev_buf,
     R->lay = runner_layout(max_lattices, max_sweeps);
     R->stream = static_cast<cudaStream_t>(stream);
     R->grid = sms * (bpsm < 1 ? 1 : bpsm);
+    R->minb = minb;
     R->timeout_ns = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
     R->stall = 0xFFFFFFFFu;
     R->have_graph = false;

@@ -211,13 +211,13 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
 }
 
 // Three-bit sum of four one-bit words (bit-sliced): returns b0 + 2 b1 + 4 b2.
-__device__ __forceinline__ void add4(uint64_t a, uint64_t b, uint64_t c, uint64_t d, uint64_t& b0, uint64_t& b1,
-                                     uint64_t& b2)
+template <typename U>
+__device__ __forceinline__ void add4(U a, U b, U c, U d, U& b0, U& b1, U& b2)
 {
-    const uint64_t s1 = a ^ b, c1 = a & b;
-    const uint64_t s2 = c ^ d, c2 = c & d;
+    const U s1 = a ^ b, c1 = a & b;
+    const U s2 = c ^ d, c2 = c & d;
     b0 = s1 ^ s2;
-    const uint64_t c3 = s1 & s2;
+    const U c3 = s1 & s2;
     b1 = c1 ^ c2 ^ c3;
     b2 = (c1 & c2) | (c1 & c3) | (c2 & c3);
 }
@@ -236,6 +236,11 @@ struct BcPhase {
 // word 1 picks the proposal among the two other values, and the move is
 // accepted iff the table entry for (s, proposal, h) is 2^32 or word 0 is
 // below it.  s_thr is the 54-entry table in shared memory.
+//
+// Every plane is first shifted right by the row's colour parity, so the 32
+// active sites sit at the even bit positions, and each 32-bit half is handled
+// in turn.  The fused bond sum (colour 1) adds s' * h per active site, h the
+// final neighbour sum (its four neighbours are colour 0 and already final).
 template <bool OBS, bool CG>
 __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const unsigned long long* s_thr,
                                         uint64_t item, int lane, PhaseAcc& acc)
@@ -256,51 +261,60 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
     if (lane == 0 || j == 0) left = ld<CG>(row + (j == 0 ? a.W - 1 : j - 1));
     if (lane == 31 || j + 1 == a.W) right = ld<CG>(row + (j + 1 == a.W ? 0 : j + 1));
 
-    // Neighbour planes: n (nonzero) and g (negative).
-    const uint64_t nw = (c.x << 1) | (left.x >> 63), gw = (c.y << 1) | (left.y >> 63);
-    const uint64_t ne = (c.x >> 1) | (right.x << 63), ge = (c.y >> 1) | (right.y << 63);
-    uint64_t p0, p1, p2, q0, q1, q2;
-    add4(vn.x & ~vn.y, vs.x & ~vs.y, nw & ~gw, ne & ~ge, p0, p1, p2);  // +1 neighbours
-    add4(vn.x & vn.y, vs.x & vs.y, nw & gw, ne & ge, q0, q1, q2);      // -1 neighbours
-
     const uint32_t p = (y + a.colour) & 1u;
-    const uint64_t base = (uint64_t)y * a.L + (uint64_t)j * 64u;
-    const uint32_t base_lo = (uint32_t)base;
-    const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
-    uint64_t nn = c.x, gg = c.y;
-#pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t b = 2u * k + p;
-        const uint32_t sn = (uint32_t)(c.x >> b) & 1u, sg = (uint32_t)(c.y >> b) & 1u;
-        const uint32_t sidx = sn ? (sg ? 0u : 2u) : 1u;  // s + 1
-        const uint32_t P = ((uint32_t)(p0 >> b) & 1u) | (((uint32_t)(p1 >> b) & 1u) << 1) |
-                           (((uint32_t)(p2 >> b) & 1u) << 2);
-        const uint32_t Nn = ((uint32_t)(q0 >> b) & 1u) | (((uint32_t)(q1 >> b) & 1u) << 1) |
-                            (((uint32_t)(q2 >> b) & 1u) << 2);
-        const uint32_t h4 = 4u + P - Nn;
-        const uint2 r = philox_site_w01(base_lo + b, pc, rk);
-        const uint32_t bp = r.y & 1u;
-        const uint32_t mv = sidx * 2u + bp;
-        if ((unsigned long long)r.x < s_thr[mv * 9u + h4]) {
-            const uint32_t code = (kBcNewCode >> (2u * mv)) & 3u;
-            const uint64_t bit = 1ull << b;
-            nn = (nn & ~bit) | ((uint64_t)(code & 1u) << b);
-            gg = (gg & ~bit) | ((uint64_t)(code >> 1) << b);
-        }
+    // Planes in the shifted frame (active sites at even positions).  The
+    // neighbour sum of a site is h = P - N: P (N) counts its +1 (-1)
+    // neighbours, kept as three bit-sliced 64-bit words each.
+    const uint64_t Cn = c.x >> p, Cg = c.y >> p;
+    uint64_t P0, P1, P2, N0, N1, N2;
+    {
+        const uint64_t nn_ = vn.x >> p, ng_ = vn.y >> p, sn_ = vs.x >> p, sg_ = vs.y >> p;
+        const uint64_t wn_ = ((c.x << 1) | (left.x >> 63)) >> p, wg_ = ((c.y << 1) | (left.y >> 63)) >> p;
+        const uint64_t en_ = ((c.x >> 1) | (right.x << 63)) >> p, eg_ = ((c.y >> 1) | (right.y << 63)) >> p;
+        add4<uint64_t>(nn_ & ~ng_, sn_ & ~sg_, wn_ & ~wg_, en_ & ~eg_, P0, P1, P2);
+        add4<uint64_t>(nn_ & ng_, sn_ & sg_, wn_ & wg_, en_ & eg_, N0, N1, N2);
     }
+
+    const uint64_t base = (uint64_t)y * a.L + (uint64_t)j * 64u;
+    const uint32_t site0 = (uint32_t)base + p;  // site of shifted position 0
+    const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
+    uint64_t acc_m = 0, acc_n = 0, acc_g = 0;  // accepted sites, their new n and g bits (shifted frame)
+    int bsum = 0;                              // sum over active sites of s' * h (fused bond sum)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int hs = 32 * half;
+        const uint32_t cn = (uint32_t)(Cn >> hs), cg = (uint32_t)(Cg >> hs);
+        const uint32_t p0 = (uint32_t)(P0 >> hs), p1 = (uint32_t)(P1 >> hs), p2 = (uint32_t)(P2 >> hs);
+        const uint32_t q0 = (uint32_t)(N0 >> hs), q1 = (uint32_t)(N1 >> hs), q2 = (uint32_t)(N2 >> hs);
+        uint32_t am = 0, an = 0, ag = 0;
+#pragma unroll 2
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t b = 2u * k;
+            const uint32_t s_n = (cn >> b) & 1u, s_g = (cg >> b) & 1u;
+            const uint32_t sidx = s_n ? (s_g ? 0u : 2u) : 1u;  // s + 1
+            const uint32_t P = ((p0 >> b) & 1u) | (((p1 >> b) & 1u) << 1) | (((p2 >> b) & 1u) << 2);
+            const uint32_t N = ((q0 >> b) & 1u) | (((q1 >> b) & 1u) << 1) | (((q2 >> b) & 1u) << 2);
+            const uint2 r = philox_site_w01(site0 + (uint32_t)hs + b, pc, rk);
+            const uint32_t mv = sidx * 2u + (r.y & 1u);
+            int sv = (int)sidx - 1;
+            if ((unsigned long long)r.x < s_thr[mv * 9u + 4u + P - N]) {
+                const uint32_t code = (kBcNewCode >> (2u * mv)) & 3u;
+                am |= 1u << b;
+                an |= (code & 1u) << b;
+                ag |= (code >> 1) << b;
+                sv = (int)(code & 1u) * (1 - 2 * (int)(code >> 1));
+            }
+            if constexpr (OBS) bsum += sv * ((int)P - (int)N);
+        }
+        acc_m |= (uint64_t)am << hs;
+        acc_n |= (uint64_t)an << hs;
+        acc_g |= (uint64_t)ag << hs;
+    }
+    const uint64_t m = acc_m << p;
+    const uint64_t nn = (c.x & ~m) | (acc_n << p), gg = (c.y & ~m) | (acc_g << p);
     row[j] = make_ulonglong2(nn, gg);
     acc.D += 32;
-
     if constexpr (OBS) {
-        const uint64_t amask = kEvenBits << p;
-        const uint64_t na = nn & amask;
-        const uint64_t nbn[4] = {vn.x, vs.x, nw, ne}, nbg[4] = {vn.y, vs.y, gw, ge};
-        long long bsum = 0;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const uint64_t both = na & nbn[d];
-            bsum += __popcll(both) - 2 * __popcll(both & (gg ^ nbg[d]));
-        }
         acc.B += bsum;
         acc.M += __popcll(nn & ~gg) - __popcll(nn & gg);
         acc.Q += __popcll(nn);
