@@ -1,0 +1,88 @@
+"""Physics of the verified CUDA path at sizes the oracle cannot reach.
+
+* Onsager: u(Tc) = -sqrt(2) in the thermodynamic limit; on the L = 1024
+  torus Kaufman's exact finite-size energy applies.  At Tc, equilibrium is
+  approached from below by an ordered start and from above by a random
+  start; both time averages must lie within 5e-3 of the exact value.
+  (Relaxation at Tc is slow, which is why the tolerance is a few 1e-3.)
+* Below Tc (0.9 Tc) an ordered start equilibrates fast and matches
+  Onsager's closed form to 2e-3.
+* Schwinger-Dyson, Eq. (3): after 128 sweeps from a quench the identity
+  holds to within a few 1e-3 (the paper reports deviations of order 1e-4 on
+  far larger lattices), for Ising at Tc and Blume-Capel at (Delta, T) =
+  (1, 1.398).
+* The draw count per sweep (the roofline's work count) equals the number of
+  uphill sites counted directly from the oracle's states.
+"""
+import numpy as np
+import pytest
+
+import physics as ph
+from paper_2502_18624_gb300 import binding as b
+
+pytestmark = pytest.mark.gpu
+TC = b.TC_ISING
+
+
+def _mean_energy(start, L, T, sweeps, discard, seed):
+    lat = b.Lattice(0, L, T, seed)
+    if start == "ordered":
+        lat.set_spins(np.ones((L, L), dtype=np.int8))
+    e = []
+    done = 0
+    while done < sweeps:
+        n = min(1024, sweeps - done)
+        obs = lat.sweep(n)
+        e.append(-obs["B"].astype(np.float64) / (L * L))
+        done += n
+    lat.close()
+    return float(np.concatenate(e)[discard:].mean())
+
+
+def test_energy_at_tc_brackets_the_exact_finite_torus_value(gpu):
+    L = 1024
+    u = ph.kaufman_u(L, TC)
+    assert abs(u + np.sqrt(2.0)) < 2e-3          # already close to Onsager's -sqrt(2)
+    e_ord = _mean_energy("ordered", L, TC, 32768, 16384, 11)
+    e_rnd = _mean_energy("random", L, TC, 32768, 16384, 12)
+    assert e_ord <= u + 1e-3 and e_rnd >= u - 1e-3, (e_ord, u, e_rnd)
+    assert abs(e_ord - u) < 5e-3 and abs(e_rnd - u) < 5e-3, (e_ord, u, e_rnd)
+
+
+def test_energy_below_tc_matches_onsager(gpu):
+    T = 0.9 * TC
+    e = _mean_energy("ordered", 512, T, 4096, 1024, 13)
+    assert abs(e - ph.onsager_u(T)) < 2e-3, (e, ph.onsager_u(T))
+
+
+@pytest.mark.parametrize("model,L,T,Delta", [(0, 4096, TC, 0.0), (1, 4096, 1.398, 1.0)])
+def test_schwinger_dyson_after_128_sweeps(gpu, orc, model, L, T, Delta):
+    lat = b.Lattice(model, L, T, 128, Delta=Delta)
+    lat.sweep(128, record=False)
+    sd = orc.sd_value(lat.sd_hist(), 1.0, T)
+    lat.close()
+    assert abs(sd - 1.0) < 5e-3, sd
+
+
+def _uphill(s, colour):
+    """Sites of `colour` whose flip costs energy (s*h > 0), from an int8 state."""
+    h = np.roll(s, 1, 0) + np.roll(s, -1, 0) + np.roll(s, 1, 1) + np.roll(s, -1, 1)
+    y, x = np.indices(s.shape)
+    return int(np.sum(((x + y) % 2 == colour) & (s * h > 0)))
+
+
+def test_draw_count_equals_uphill_sites(gpu, orc):
+    L, seed, T = 256, 3, TC
+    lat = b.Lattice(0, L, T, seed)
+    thr = orc.thresholds(0, 1.0, T)
+    s = orc.init(0, L, seed)
+    for t in range(5):
+        before = s.copy()
+        obs = lat.sweep(1)
+        orc.sweep(0, s, seed, thr, t)
+        # phase 0 sees the state before the sweep; phase 1 sees colour-0 sites already updated
+        mid = before.copy()
+        y, x = np.indices(s.shape)
+        mid[(x + y) % 2 == 0] = s[(x + y) % 2 == 0]
+        assert int(obs["draws"][0]) == _uphill(before, 0) + _uphill(mid, 1)
+    lat.close()
