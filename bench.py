@@ -248,11 +248,11 @@ def native(args, wl):
     achieved = OPS_PER_DRAW * draws_per_launch / launch_s / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and not args.L:
         try:
             with open(prof) as f:
-                tr = json.load(f)
-            if tr.get("workload") == args.workload and tr.get("kernel_rev") == kernel_rev():
+                tr = json.load(f).get(args.workload, {})
+            if tr.get("kernel_rev") == kernel_rev():
                 traffic = tr.get("bytes_per_launch")
         except Exception:
             traffic = None
@@ -376,7 +376,7 @@ def measured_hbm_gbs() -> float:
 def kernel_rev() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("k_sweep.cu", "philox.cuh", "lat_internal.cuh"):
+    for name in ("k_sweep.cu", "sweep_item.cuh", "philox.cuh", "lat_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2502_18624_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
