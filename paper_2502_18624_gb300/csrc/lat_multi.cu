@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
 {
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
-    __shared__ unsigned long long s_thr[54];
+    __shared__ unsigned long long s_thr[72];
     const unsigned long long total = ctl->total;
     const uint32_t K = ctl->nphases;
     for (;;) {
@@ -163,8 +163,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
             if (*(volatile unsigned int*)&ctl->error) stop = 1;
             s_stop = stop;
         }
-        if (d.model == 1)
-            for (int i = threadIdx.x; i < 54; i += blockDim.x) s_thr[i] = d.bc_thr[i];
+        if (d.model == 1) bc_table72(d.bc_thr, s_thr);
         __syncthreads();
         if (s_stop) break;
 

@@ -222,9 +222,32 @@ __device__ __forceinline__ void add4(U a, U b, U c, U d, U& b0, U& b1, U& b2)
     b2 = (c1 & c2) | (c1 & c3) | (c2 & c3);
 }
 
-// New (n, g) code after accepting the proposal: index (s+1)*2 + b, two bits
-// (n | g << 1) per entry.  s=-1: {0, +1}; s=0: {-1, +1}; s=+1: {-1, 0}.
-constexpr uint32_t kBcNewCode = (0u << 0) | (1u << 2) | (3u << 4) | (1u << 6) | (3u << 8) | (0u << 10);
+// A Blume-Capel spin's 2-bit code is n | g << 1 (n: s != 0, g: s = -1):
+// 0 for s = 0, 1 for s = +1, 3 for s = -1 (2 never occurs).  The kernels
+// index their acceptance table by (code, proposal bit b, h + 4):
+// entry (code*2 + b)*9 + h+4, 72 entries with code 2 unused; see
+// bc_table72.  kBcNext gives the code of the proposed value, the b-th of the
+// two other values in ascending order, at index code*2 + b (2 bits each):
+// s=0 -> {-1, +1}, s=+1 -> {-1, 0}, s=-1 -> {0, +1}.
+constexpr uint32_t kBcNext = (3u << 0) | (1u << 2) | (3u << 4) | (0u << 6) | (0u << 8) | (0u << 10) |
+                             (0u << 12) | (1u << 14);
+
+// Expand the 54-entry table (index ((s+1)*2 + b)*9 + h+4) to the 72-entry
+// code-indexed one, in shared memory.
+__device__ __forceinline__ void bc_table72(const unsigned long long* thr54, unsigned long long* s_thr)
+{
+    for (int i = threadIdx.x; i < 72; i += blockDim.x) {
+        const int code = i / 18, b = (i / 9) % 2, h = i % 9;
+        const int s = code == 0 ? 0 : (code == 1 ? 1 : -1);
+        s_thr[i] = code == 2 ? 0ull : thr54[((s + 1) * 2 + b) * 9 + h];
+    }
+}
+
+// Value of a 2-bit spin code: 0, +1 or -1.
+__device__ __forceinline__ int bc_value(uint32_t code)
+{
+    return (int)(code & 1u) * (1 - (int)(code & 2u));
+}
 
 struct BcPhase {
     ulonglong2* spins;  // L rows of W (n, g) word pairs
@@ -235,7 +258,8 @@ struct BcPhase {
 // Blume-Capel decision (Eq. (2)): every active site draws; the low bit of
 // word 1 picks the proposal among the two other values, and the move is
 // accepted iff the table entry for (s, proposal, h) is 2^32 or word 0 is
-// below it.  s_thr is the 54-entry table in shared memory.
+// below it.  s_thr is the 72-entry code-indexed table (bc_table72) in shared
+// memory; the update is branch-free.
 //
 // Every plane is first shifted right by the row's colour parity, so the 32
 // active sites sit at the even bit positions, and each 32-bit half is handled
@@ -290,21 +314,18 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
 #pragma unroll 2
         for (int k = 0; k < 16; ++k) {
             const uint32_t b = 2u * k;
-            const uint32_t s_n = (cn >> b) & 1u, s_g = (cg >> b) & 1u;
-            const uint32_t sidx = s_n ? (s_g ? 0u : 2u) : 1u;  // s + 1
+            const uint32_t code = ((cn >> b) & 1u) | (((cg >> b) & 1u) << 1);
             const uint32_t P = ((p0 >> b) & 1u) | (((p1 >> b) & 1u) << 1) | (((p2 >> b) & 1u) << 2);
             const uint32_t N = ((q0 >> b) & 1u) | (((q1 >> b) & 1u) << 1) | (((q2 >> b) & 1u) << 2);
             const uint2 r = philox_site_w01(site0 + (uint32_t)hs + b, pc, rk);
-            const uint32_t mv = sidx * 2u + (r.y & 1u);
-            int sv = (int)sidx - 1;
-            if ((unsigned long long)r.x < s_thr[mv * 9u + 4u + P - N]) {
-                const uint32_t code = (kBcNewCode >> (2u * mv)) & 3u;
-                am |= 1u << b;
-                an |= (code & 1u) << b;
-                ag |= (code >> 1) << b;
-                sv = (int)(code & 1u) * (1 - 2 * (int)(code >> 1));
-            }
-            if constexpr (OBS) bsum += sv * ((int)P - (int)N);
+            const uint32_t mv = code * 2u + (r.y & 1u);
+            const bool accept = (unsigned long long)r.x < s_thr[mv * 9u + 4u + P - N];
+            const uint32_t next = (kBcNext >> (2u * mv)) & 3u;
+            const uint32_t bit = accept ? (1u << b) : 0u;
+            am |= bit;
+            an |= (next & 1u) ? bit : 0u;
+            ag |= (next & 2u) ? bit : 0u;
+            if constexpr (OBS) bsum += bc_value(accept ? next : code) * ((int)P - (int)N);
         }
         acc_m |= (uint64_t)am << hs;
         acc_n |= (uint64_t)an << hs;
