@@ -58,6 +58,10 @@ def _bind(lib):
         "or_pack": (None, [i32, u32, P, P]),
         "or_hash_words": (u64, [P, u64]),
         "or_hash": (u64, [i32, u32, P]),
+        "or_lut_table": (None, [f64, f64, P]),
+        "or_sweep_lut": (None, [u32, u64, P, u32, P]),
+        "or_run_lut": (None, [u32, u64, P, u32, u32, P, P]),
+        "or_lut_word": (u32, [u64, P, u64, u32, u32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,3 +208,29 @@ def energy(model: int, obs, J: float = 1.0, Delta: float = 0.0) -> float:
     """E = -J B + Delta Q from exact (M, B, Q) integers (Eqs. (1)-(2))."""
     _, B, Q = obs
     return -J * float(B) + (Delta * float(Q) if model == 1 else 0.0)
+
+
+# ---- the paper's lookup-table random bits (Ising, section 3.2) ----------------
+
+def lut_table(J: float, T: float) -> np.ndarray:
+    t = np.zeros(16, dtype=np.uint32)
+    _load().or_lut_table(J, T, _p(t))
+    return t
+
+
+def sweep_lut(s: np.ndarray, seed: int, tbl: np.ndarray, t: int) -> np.ndarray:
+    tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
+    _load().or_sweep_lut(s.shape[0], seed, _p(tbl), t, _p(s))
+    return s
+
+
+def run_lut(s: np.ndarray, seed: int, tbl: np.ndarray, first: int, n: int, record: bool = True):
+    tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
+    obs = np.zeros((n, 3), dtype=np.int64) if record else None
+    _load().or_run_lut(s.shape[0], seed, _p(tbl), first, n, _p(s), _p(obs) if record else None)
+    return obs
+
+
+def lut_word(seed: int, tbl: np.ndarray, w: int, t: int, colour: int, which: int) -> int:
+    tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
+    return int(_load().or_lut_word(seed, _p(tbl), w, t, colour, which))

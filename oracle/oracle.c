@@ -29,6 +29,11 @@
  *                      bond identity B = Cx(1) + Cy(1).
  *   or_sd_hist         Eq. (3) equals 1 exactly under the enumerated
  *                      Boltzmann weights.
+ *   or_lut_table       80-digit closed form of the cumulative pattern
+ *                      probabilities (tests/test_oracle_lut.py).
+ *   or_sweep_lut       Kaufman's exact finite-torus energy and Onsager's
+ *                      energy reproduced by long runs; frequencies of the
+ *                      generated bits; +-flip symmetry.
  *   or_pack/or_hash    numpy.packbits for the packing; the mixing function is
  *                      a fixed bijection, so the hash is "parity unpinned"
  *                      beyond the packing (it only compares two lattices).
@@ -251,6 +256,103 @@ void or_sweep_strip(int model, uint32_t L, uint64_t seed, const uint64_t* thr, u
             }
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's lookup-table random bits for the Ising model (section 3.2).   */
+/* A word of random bits, each set independently with probability           */
+/* p = exp(-4 J / T), is produced four bits at a time: a uniform 32-bit u    */
+/* is located in a sorted table of 16 entries, and the index of the largest  */
+/* entry not above u is itself the four bits.  Table: tbl[j] = floor(2^32 *  */
+/* sum over patterns m < j of p^popcount(m) (1-p)^(4-popcount(m))), so index */
+/* j comes out with probability of pattern j (to within 2^-32).  A site with */
+/* all four neighbours equal to it flips iff its bit in one such word AND    */
+/* its bit in a second, independent word are set (probability p^2 =          */
+/* exp(-8J/T)); with exactly three iff its bit in the first word is set;     */
+/* every other site flips.  (The paper defers the table construction to a    */
+/* companion reference; the construction above is this library's reading.)  */
+/*                                                                           */
+/* Stream: the 64-bit word w = y*(L/64) + x/64 draws, in sweep t and colour  */
+/* phase c, the Philox blocks at counters (4w+q low, 4w+q high, t, c+2),     */
+/* q = 0..3; uniform i = 4q + k is word k of block q.  Uniforms 0..7 give    */
+/* the first word of bits, uniforms 8..15 the second, lookup l giving bits   */
+/* 4l .. 4l+3.  The word's active sites (those of colour c, in increasing x) */
+/* take bits 0..31 in order.                                                 */
+/* ------------------------------------------------------------------------ */
+void or_lut_table(double J, double T, uint32_t tbl[16])
+{
+    double p = exp(-4.0 * J / T);
+    double cum = 0.0;
+    for (int j = 0; j < 16; ++j) {
+        double v = floor(ldexp(cum, 32));
+        tbl[j] = v >= 4294967295.0 ? 4294967295u : (uint32_t)v;
+        int k = __builtin_popcount((unsigned)j);
+        cum += pow(p, k) * pow(1.0 - p, 4 - k);
+    }
+}
+
+static int or_lut_index(const uint32_t tbl[16], uint32_t u)
+{
+    int best = 0;
+    for (int j = 0; j < 16; ++j)
+        if (tbl[j] <= u) best = j;
+    return best;
+}
+
+/* Bit `bit` (0..31) of random word `which` (0 or 1) of the word w. */
+static int or_lut_bit(uint64_t seed, const uint32_t tbl[16], uint64_t w, uint32_t sweep, uint32_t colour,
+                      int which, int bit)
+{
+    int i = 8 * which + bit / 4;              /* uniform index 0..15 */
+    uint64_t ctr = 4 * w + (uint64_t)(i / 4);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c[4] = {(uint32_t)ctr, (uint32_t)(ctr >> 32), sweep, colour + 2u};
+    uint32_t out[4];
+    or_philox4x32_10(c, key, out);
+    int j = or_lut_index(tbl, out[i % 4]);
+    return (j >> (bit % 4)) & 1;
+}
+
+void or_sweep_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t sweep, int8_t* s)
+{
+    for (uint32_t colour = 0; colour < 2; ++colour)
+        for (uint64_t y = 0; y < L; ++y)
+            for (uint64_t x = 0; x < L; ++x) {
+                if (((x + y) & 1u) != colour) continue;
+                uint64_t site = y * L + x;
+                int sv = s[site];
+                int agree = (s[((y + L - 1) % L) * L + x] == sv) + (s[((y + 1) % L) * L + x] == sv) +
+                            (s[y * L + (x + L - 1) % L] == sv) + (s[y * L + (x + 1) % L] == sv);
+                uint64_t w = y * (L / 64) + x / 64;
+                int k = (int)((x % 64) / 2); /* rank of x among the word's colour-c sites */
+                int flip;
+                if (agree == 4)
+                    flip = or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 0, k) &
+                           or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 1, k);
+                else if (agree == 3)
+                    flip = or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 0, k);
+                else
+                    flip = 1;
+                if (flip) s[site] = (int8_t)(-sv);
+            }
+}
+
+/* Several lookup-table sweeps, recording (M, B, Q) after each when obs != NULL. */
+void or_run_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t first_sweep, uint32_t nsweeps,
+                int8_t* s, int64_t* obs)
+{
+    for (uint32_t i = 0; i < nsweeps; ++i) {
+        or_sweep_lut(L, seed, tbl, first_sweep + i, s);
+        if (obs) or_measure(0, L, s, obs + 3 * (size_t)i);
+    }
+}
+
+/* Random bit words for tests: bits of word `which` for the word w. */
+uint32_t or_lut_word(uint64_t seed, const uint32_t tbl[16], uint64_t w, uint32_t sweep, uint32_t colour, int which)
+{
+    uint32_t v = 0;
+    for (int b = 0; b < 32; ++b) v |= (uint32_t)or_lut_bit(seed, tbl, w, sweep, colour, which, b) << b;
+    return v;
 }
 
 /* ------------------------------------------------------------------------ */

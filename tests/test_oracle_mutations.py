@@ -86,6 +86,20 @@ def _init_fails(orc):
     return np.max(np.abs(frac - 1 / 3)) > 0.01
 
 
+def _lut_energy_fails(orc):
+    import test_oracle_lut as tl
+    mean, err = tl._energy(orc, 64, 0.9 * ph.TC, 17, 1500, 300, True)
+    return abs(mean - ph.kaufman_u(64, 0.9 * ph.TC)) > 4 * err + 1e-4
+
+
+def _lut_table_fails(orc):
+    import mpmath
+    p = mpmath.exp(-4 / mpmath.mpf(ph.TC))
+    tbl = orc.lut_table(1.0, ph.TC)
+    cum = p**0 * (1 - p) ** 4  # probability of pattern 0
+    return abs(int(tbl[1]) - int(mpmath.floor(mpmath.ldexp(cum, 32)))) > 1 or int(tbl[0]) != 0
+
+
 MUTATIONS = [
     ("sweep drops the east neighbour",
      "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
@@ -108,6 +122,13 @@ MUTATIONS = [
      "ay += v * s[((y + r + 1) % L) * L + x];", _corr_fails),
     ("threshold rounded up", "double v = floor(ldexp(exp(-dE / T), 32));",
      "double v = ceil(ldexp(exp(-dE / T), 32));", _thr_fails),
+    ("lookup-table 4-agree flip uses one word instead of two",
+     "                    flip = or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 0, k) &\n                           or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 1, k);",
+     "                    flip = or_lut_bit(seed, tbl, w, (uint32_t)sweep, colour, 0, k);", _lut_energy_fails),
+    ("lookup table built from the next pattern's cumulative probability",
+     "        double v = floor(ldexp(cum, 32));\n        tbl[j]",
+     "        int kk = __builtin_popcount((unsigned)j);\n        double v = floor(ldexp(cum + pow(exp(-4.0 * J / T), kk) * pow(1.0 - exp(-4.0 * J / T), 4 - kk), 32));\n        tbl[j]",
+     _lut_table_fails),
     ("Blume-Capel quench not uniform over three values",
      "s[site] = (int8_t)((int)(((uint64_t)w[0] * 3u) >> 32) - 1);",
      "s[site] = (int8_t)((int)(((uint64_t)w[0] * 2u) >> 32) - 1);", _init_fails),
