@@ -54,6 +54,9 @@ WORKLOADS = {
                         name="ising-2d L=131072 T=0.9Tc seed=7: K sweeps, E/M every sweep, C(r<=1024) at sweeps 2^k"),
     "ising-capacity": dict(model=0, L=1 << 19, T=TC, Delta=0.0, seed=7, rmax=1024,
                            name="ising-2d L=524288 (2^38 spins, 32 GiB) T=Tc seed=7: K sweeps, E/M every sweep"),
+    "ising-lut": dict(model=0, L=1 << 17, T=TC, Delta=0.0, seed=7, rmax=1024, rng=1,
+                      name="ising-2d L=131072 T=Tc seed=7, the paper's lookup-table random bits: K sweeps, E/M every "
+                           "sweep, C(r<=1024) x/y at sweeps 2^k"),
     "bc": dict(model=1, L=1 << 16, T=1.398, Delta=1.0, seed=99, rmax=512,
                name="blume-capel L=65536 Delta=1 T=1.398 seed=99: K sweeps, E/M/Q every sweep, C(r<=512) at sweeps 2^k"),
 }
@@ -209,7 +212,8 @@ def native(args, wl):
     stream = torch.cuda.current_stream(device)
     seed = wl["seed"] + rank
     K, W = args.steps, args.warmup
-    mk = lambda: b.Lattice(wl["model"], wl["L"], wl["T"], seed, Delta=wl["Delta"], stream=stream, device=device)
+    mk = lambda: b.Lattice(wl["model"], wl["L"], wl["T"], seed, Delta=wl["Delta"], stream=stream, device=device,
+                           rng=wl.get("rng", 0))
 
     # warm-up sweeps (kernels, module load, clocks), then a fresh quench for the timed job
     lat = mk()
@@ -258,7 +262,8 @@ def native(args, wl):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "T IMAD-ops/s",
                 "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
-                "kernel": "k_ising_phase" if wl["model"] == 0 else "k_bc_phase",
+                "kernel": ("k_ising_phase_lut" if wl.get("rng") else "k_ising_phase") if wl["model"] == 0
+                          else "k_bc_phase",
                 "launch_ms": launch_s * 1e3, "draws_per_launch": draws_per_launch,
                 "ops_per_draw": OPS_PER_DRAW,
                 "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "

@@ -53,6 +53,10 @@ extern "C" {
 #define LAT_ISING 0
 #define LAT_BLUME_CAPEL 1
 
+/* Random-number modes (lat_params.rng). */
+#define LAT_RNG_SITE 0  /* one Philox4x32-10 block per decision, counter (site, sweep, colour) */
+#define LAT_RNG_TABLE 1 /* Ising only: the paper's lookup-table random bits (section 3.2) */
+
 /* Largest accepted linear size: 2^20 (2^40 spins, 128 GiB as Ising). */
 #define LAT_MAX_L (1u << 20)
 
@@ -64,7 +68,19 @@ typedef struct lat lat_t; /* opaque; owned by the library */
  *   J      ferromagnetic coupling, J > 0 (section 2 takes J > 0).
  *   Delta  crystal-field coupling of Eq. (2); ignored for Ising.
  *   T      temperature, T > 0 (k_B = 1).
- *   seed   64-bit key of the random stream. */
+ *   seed   64-bit key of the random stream.
+ *   rng    LAT_RNG_SITE (default) or LAT_RNG_TABLE.  LAT_RNG_TABLE (Ising
+ *          only) draws the flips of section 3.2: per 64-bit word and phase,
+ *          two words of independent random bits with P(1) = p = exp(-4J/T),
+ *          each made four bits at a time by locating a 32-bit uniform in a
+ *          sorted 16-entry table (lat_lut_table); a site with four equal
+ *          neighbours flips iff both words' bits are set (probability p^2),
+ *          with three iff the first word's bit is set, otherwise always.
+ *          Uniforms: word w = y*(L/64) + x/64 uses Philox blocks at counters
+ *          (4w+q low, 4w+q high, sweep, colour+2), q = 0..3; uniform 4q+k is
+ *          word k of block q; uniforms 0..7 make the first bit word and 8..15
+ *          the second, four bits per uniform; the word's active sites take
+ *          bits 0..31 in increasing x. */
 typedef struct {
     int32_t model;
     uint32_t L;
@@ -72,6 +88,7 @@ typedef struct {
     double Delta;
     double T;
     uint64_t seed;
+    int32_t rng;
 } lat_params;
 
 /* Exact observables after a sweep (Eqs. (1)-(2)):
@@ -104,6 +121,14 @@ size_t lat_footprint(const lat_params* p);
  * for the move from s to the b-th other value (ascending) with neighbour
  * sum h.  n must be >= 5 (Ising) or >= 54 (BC), else LAT_EINVAL.  Host only. */
 int lat_thresholds(const lat_params* p, uint64_t* out, size_t n);
+
+/* The 16-entry table of LAT_RNG_TABLE for p: entry j = floor(2^32 * sum
+ * over 4-bit patterns m < j of p^popcount(m) (1-p)^(4-popcount(m))),
+ * p = exp(-4J/T), clamped to 2^32-1; a uniform u selects the largest j with
+ * entry j <= u, and j is the four random bits.  (The paper leaves the
+ * construction to a companion reference; this is the library's reading.)
+ * Host only; LAT_EINVAL unless p describes an Ising lattice. */
+int lat_lut_table(const lat_params* p, uint32_t out[16]);
 
 /* Create a lattice and draw its initial quench (infinite-temperature start,
  * section 1) on the device.

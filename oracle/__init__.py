@@ -62,6 +62,7 @@ def _bind(lib):
         "or_sweep_lut": (None, [u32, u64, P, u32, P]),
         "or_run_lut": (None, [u32, u64, P, u32, u32, P, P]),
         "or_lut_word": (u32, [u64, P, u64, u32, u32, i32]),
+        "or_sweep_strip_lut": (None, [u32, u64, P, u32, u64, u32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -234,3 +235,11 @@ def run_lut(s: np.ndarray, seed: int, tbl: np.ndarray, first: int, n: int, recor
 def lut_word(seed: int, tbl: np.ndarray, w: int, t: int, colour: int, which: int) -> int:
     tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
     return int(_load().or_lut_word(seed, _p(tbl), w, t, colour, which))
+
+
+def sweep_strip_lut(L: int, seed: int, tbl: np.ndarray, t: int, y0: int, strip: np.ndarray) -> np.ndarray:
+    H = strip.shape[0] - 4
+    assert strip.shape == (H + 4, L) and strip.dtype == np.int8
+    tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
+    _load().or_sweep_strip_lut(L, seed, _p(tbl), t, y0, H, _p(strip))
+    return strip

@@ -337,6 +337,38 @@ void or_sweep_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t sw
             }
 }
 
+/* The lookup-table sweep restricted to a strip (as or_sweep_strip): strip  */
+/* holds the H+4 full rows y0-2 .. y0+H+1 (mod L); rows 2..H+1 become the    */
+/* global rows y0..y0+H-1 after the sweep.                                   */
+void or_sweep_strip_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t sweep, uint64_t y0,
+                        uint32_t H, int8_t* strip)
+{
+    for (uint32_t colour = 0; colour < 2; ++colour) {
+        uint32_t r_lo = colour == 0 ? 1 : 2;
+        uint32_t r_hi = colour == 0 ? H + 3 : H + 2;
+        for (uint32_t r = r_lo; r < r_hi; ++r) {
+            uint64_t y = (y0 + (uint64_t)L * 4 + r - 2) % L;
+            int8_t* row = strip + (size_t)r * L;
+            for (uint64_t x = 0; x < L; ++x) {
+                if (((x + y) & 1u) != colour) continue;
+                int sv = row[x];
+                int agree = (strip[(size_t)(r - 1) * L + x] == sv) + (strip[(size_t)(r + 1) * L + x] == sv) +
+                            (row[(x + L - 1) % L] == sv) + (row[(x + 1) % L] == sv);
+                uint64_t w = y * (L / 64) + x / 64;
+                int k = (int)((x % 64) / 2);
+                int flip;
+                if (agree == 4)
+                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k) & or_lut_bit(seed, tbl, w, sweep, colour, 1, k);
+                else if (agree == 3)
+                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k);
+                else
+                    flip = 1;
+                if (flip) row[x] = (int8_t)(-sv);
+            }
+        }
+    }
+}
+
 /* Several lookup-table sweeps, recording (M, B, Q) after each when obs != NULL. */
 void or_run_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t first_sweep, uint32_t nsweeps,
                 int8_t* s, int64_t* obs)

@@ -17,6 +17,7 @@ from . import _build
 
 LAT_OK, LAT_EINVAL, LAT_ENOMEM, LAT_ECUDA, LAT_ETIMEDOUT, LAT_ESTATE = 0, -1, -2, -3, -4, -5
 LAT_ISING, LAT_BLUME_CAPEL = 0, 1
+LAT_RNG_SITE, LAT_RNG_TABLE = 0, 1
 LAT_MAX_L = 1 << 20
 TC_ISING = 2.0 / np.log(1.0 + np.sqrt(2.0))
 
@@ -29,7 +30,8 @@ class LatError(RuntimeError):
 
 class lat_params(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("L", ctypes.c_uint32), ("J", ctypes.c_double),
-                ("Delta", ctypes.c_double), ("T", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("Delta", ctypes.c_double), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("rng", ctypes.c_int32)]
 
 
 class lat_obs(ctypes.Structure):
@@ -63,6 +65,7 @@ def load(build_if_missing: bool = True):
         "lat_footprint": (sz, [PP]),
         "lat_state_bytes": (sz, [PP]),
         "lat_thresholds": (i32, [PP, P, sz]),
+        "lat_lut_table": (i32, [PP, P]),
         "lat_create": (i32, [PP, P, sz, P, ctypes.POINTER(P)]),
         "lat_sweep": (i32, [P, u32, P]),
         "lat_measure": (i32, [P, P]),
@@ -105,8 +108,9 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(model: int, L: int, T: float, seed: int, J: float = 1.0, Delta: float = 0.0) -> lat_params:
-    return lat_params(int(model), int(L), float(J), float(Delta), float(T), int(seed) & (2**64 - 1))
+def make_params(model: int, L: int, T: float, seed: int, J: float = 1.0, Delta: float = 0.0,
+                rng: int = LAT_RNG_SITE) -> lat_params:
+    return lat_params(int(model), int(L), float(J), float(Delta), float(T), int(seed) & (2**64 - 1), int(rng))
 
 
 def strerror(code: int) -> str:
@@ -127,6 +131,12 @@ def lat_thresholds(p: lat_params) -> np.ndarray:
     out = np.zeros(54, dtype=np.uint64)
     _check(load().lat_thresholds(ctypes.byref(p), _ptr(out), out.size), "lat_thresholds")
     return out[: (5 if p.model == LAT_ISING else 54)].copy()
+
+
+def lat_lut_table(p: lat_params) -> np.ndarray:
+    out = np.zeros(16, dtype=np.uint32)
+    _check(load().lat_lut_table(ctypes.byref(p), _ptr(out)), "lat_lut_table")
+    return out
 
 
 def lat_create(p: lat_params, dev_buf: int | None, nbytes: int, stream: int | None) -> ctypes.c_void_p:
@@ -220,10 +230,10 @@ class Lattice:
     """One lattice on the current CUDA device, in a torch-owned buffer."""
 
     def __init__(self, model: int, L: int, T: float, seed: int, J: float = 1.0, Delta: float = 0.0,
-                 stream=None, device=None):
+                 stream=None, device=None, rng: int = LAT_RNG_SITE):
         import torch
 
-        self.params = make_params(model, L, T, seed, J, Delta)
+        self.params = make_params(model, L, T, seed, J, Delta, rng)
         self.model, self.L = int(model), int(L)
         nbytes = lat_footprint(self.params)
         if nbytes == 0:

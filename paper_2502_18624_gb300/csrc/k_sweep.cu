@@ -30,6 +30,22 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_c
     flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
 }
 
+template <int CW, bool OBS>
+__global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
+{
+    __shared__ uint32_t s_lut[16];
+    if (threadIdx.x < 16) s_lut[threadIdx.x] = a.lut[threadIdx.x];
+    __syncthreads();
+    const IsingPhase ph{a.spins, a.L, a.W, a.sweep, a.colour, a.thr4, a.thr8, a.mode4, a.mode8};
+    const uint64_t nitems = (uint64_t)a.L * (a.W / CW);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    PhaseAcc acc;
+    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems; item += stride)
+        ising_item_lut<CW, OBS, false>(ph, a.rk, s_lut, item, lane, acc);
+    flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
+}
+
 template <bool OBS>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_bc_phase(const __grid_constant__ BcPhaseArgs a)
 {
@@ -75,6 +91,16 @@ cudaError_t launch_ising_phase(const IsingPhaseArgs& a, const LaunchShape& ls, c
     const bool even_words = (a.W % 2) == 0;
     const uint64_t nitems = (uint64_t)a.L * (even_words ? a.W / 2 : a.W);
     const int grid = blocks_for(nitems, ls.sms, ls.ising_bpsm);
+    if (a.rng == LAT_RNG_TABLE_MODE) {
+        if (even_words) {
+            if (a.obs) k_ising_phase_lut<2, true><<<grid, kSweepThreads, 0, st>>>(a);
+            else k_ising_phase_lut<2, false><<<grid, kSweepThreads, 0, st>>>(a);
+        } else {
+            if (a.obs) k_ising_phase_lut<1, true><<<grid, kSweepThreads, 0, st>>>(a);
+            else k_ising_phase_lut<1, false><<<grid, kSweepThreads, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     if (even_words) {
         if (a.obs) k_ising_phase<2, true><<<grid, kSweepThreads, 0, st>>>(a);
         else k_ising_phase<2, false><<<grid, kSweepThreads, 0, st>>>(a);

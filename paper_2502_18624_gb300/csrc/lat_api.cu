@@ -37,6 +37,8 @@ bool params_ok(const lat_params* p)
     if (!(p->J > 0.0) || !std::isfinite(p->J)) return false;
     if (!(p->T > 0.0) || !std::isfinite(p->T)) return false;
     if (p->model == LAT_BLUME_CAPEL && !std::isfinite(p->Delta)) return false;
+    if (p->rng != LAT_RNG_SITE && p->rng != LAT_RNG_TABLE) return false;
+    if (p->rng == LAT_RNG_TABLE && p->model != LAT_ISING) return false;
     return true;
 }
 
@@ -95,6 +97,20 @@ size_t build_table(const lat_params* p, uint64_t* t)
     return 54;
 }
 
+// LAT_RNG_TABLE: cumulative probabilities of the 16 four-bit patterns in
+// index order, each bit independently 1 with p = exp(-4J/T).
+void build_lut(const lat_params* p, uint32_t* out)
+{
+    const double q = std::exp(-4.0 * p->J / p->T);
+    double cum = 0.0;
+    for (int j = 0; j < 16; ++j) {
+        const double scaled = std::floor(cum * 4294967296.0);
+        out[j] = scaled >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)scaled;
+        const int ones = __builtin_popcount((unsigned)j);
+        cum += std::pow(q, (double)ones) * std::pow(1.0 - q, (double)(4 - ones));
+    }
+}
+
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
 
 }  // namespace
@@ -115,6 +131,13 @@ int lat_thresholds(const lat_params* p, uint64_t* out, size_t n)
     return LAT_OK;
 }
 
+int lat_lut_table(const lat_params* p, uint32_t out[16])
+{
+    if (!params_ok(p) || !out || p->model != LAT_ISING) return LAT_EINVAL;
+    build_lut(p, out);
+    return LAT_OK;
+}
+
 int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, lat_t** out)
 {
     if (!out || !params_ok(p)) return LAT_EINVAL;
@@ -127,6 +150,7 @@ int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, l
     h->p = *p;
     h->W = p->L / 64;
     h->nthr = build_table(p, h->thr);
+    build_lut(p, h->lut);
     h->lay = layout_of(p);
     h->stream = static_cast<cudaStream_t>(stream);
     h->next_sweep = 0;
@@ -175,6 +199,8 @@ int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
         ia.thr8 = (uint32_t)(h->thr[4] >= kAlways ? 0 : h->thr[4]);
         ia.mode4 = class_mode(h->thr[3]);
         ia.mode8 = class_mode(h->thr[4]);
+        ia.rng = (uint32_t)h->p.rng;
+        std::memcpy(ia.lut, h->lut, sizeof(ia.lut));
         ia.rk = h->rk;
     } else {
         ba.spins = static_cast<ulonglong2*>(h->spins());

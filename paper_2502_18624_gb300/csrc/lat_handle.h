@@ -17,6 +17,7 @@ struct lat {
     uint32_t W;
     uint64_t thr[54];
     size_t nthr;
+    uint32_t lut[16];  // LAT_RNG_TABLE lookup table
     Layout lay;
     char* buf;
     bool owns;

@@ -9,6 +9,7 @@
 namespace latk {
 
 constexpr uint64_t kAlways = 1ull << 32;
+constexpr uint32_t LAT_RNG_TABLE_MODE = 1;  // lat_params.rng value of the lookup-table mode
 
 // Per-class acceptance mode of an integer threshold t in [0, 2^32]:
 // t == 2^32 accepts without drawing, t == 0 rejects without drawing, any
@@ -32,6 +33,8 @@ struct IsingPhaseArgs {
     uint32_t mode4, mode8;  // ClassMode of the two uphill classes
     long long* obs;         // colour-1 phase: record to accumulate (M, B, Q); else null
     long long* draws;       // counter of Philox draws to accumulate, or null
+    uint32_t rng;           // LAT_RNG_SITE or LAT_RNG_TABLE
+    uint32_t lut[16];       // LAT_RNG_TABLE lookup table
     RoundKeys rk;
 };
 

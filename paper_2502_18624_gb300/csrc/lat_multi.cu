@@ -53,6 +53,8 @@ struct MultiDesc {
     uint32_t model, L, W, cw;
     uint32_t items, tile_items, ntiles, sweep0;
     uint32_t thr4, thr8, mode4, mode8;
+    uint32_t rng, pad[3];
+    uint32_t lut[16];
     RoundKeys rk;
 };
 
@@ -81,12 +83,22 @@ __device__ __forceinline__ unsigned int load_acquire(const unsigned int* p)
 }
 
 template <bool OBS>
-__device__ __forceinline__ void ising_tile(const MultiDesc& d, uint32_t sweep, uint32_t colour, uint64_t i0,
-                                           uint64_t i1, PhaseAcc& acc)
+__device__ __forceinline__ void ising_tile(const MultiDesc& d, const uint32_t* s_lut, uint32_t sweep,
+                                           uint32_t colour, uint64_t i0, uint64_t i1, PhaseAcc& acc)
 {
     const IsingPhase ph{static_cast<uint64_t*>(d.spins), d.L, d.W, sweep, colour, d.thr4, d.thr8, d.mode4, d.mode8};
     const RoundKeys rk = d.rk;
     const int lane = threadIdx.x & 31;
+    if (d.rng == LAT_RNG_TABLE_MODE) {
+        if (d.cw == 2) {
+            for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x)
+                ising_item_lut<2, OBS, true>(ph, rk, s_lut, it, lane, acc);
+        } else {
+            for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x)
+                ising_item_lut<1, OBS, true>(ph, rk, s_lut, it, lane, acc);
+        }
+        return;
+    }
     if (d.cw == 2) {
         for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x) ising_item<2, OBS, true>(ph, rk, it, lane, acc);
     } else {
@@ -113,6 +125,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
     __shared__ unsigned long long s_thr[72];
+    __shared__ uint32_t s_lut[16];
     const unsigned long long total = ctl->total;
     const uint32_t K = ctl->nphases;
     for (;;) {
@@ -164,6 +177,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
             s_stop = stop;
         }
         if (d.model == 1) bc_table72(d.bc_thr, s_thr);
+        else if (d.rng == LAT_RNG_TABLE_MODE && threadIdx.x < 16) s_lut[threadIdx.x] = d.lut[threadIdx.x];
         __syncthreads();
         if (s_stop) break;
 
@@ -173,8 +187,8 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
         long long* rec = d.obs ? d.obs + (size_t)(k >> 1) * kObsWords : nullptr;
         PhaseAcc acc;
         if (d.model == 0) {
-            if (colour) ising_tile<true>(d, sweep, colour, i0, i1, acc);
-            else ising_tile<false>(d, sweep, colour, i0, i1, acc);
+            if (colour) ising_tile<true>(d, s_lut, sweep, colour, i0, i1, acc);
+            else ising_tile<false>(d, s_lut, sweep, colour, i0, i1, acc);
         } else {
             if (colour) bc_tile<true>(d, s_thr, sweep, colour, i0, i1, acc);
             else bc_tile<false>(d, s_thr, sweep, colour, i0, i1, acc);
@@ -433,6 +447,8 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
             d.thr8 = (uint32_t)(h->thr[4] >= kAlways ? 0 : h->thr[4]);
             d.mode4 = class_mode(h->thr[3]);
             d.mode8 = class_mode(h->thr[4]);
+            d.rng = (uint32_t)h->p.rng;
+            std::memcpy(d.lut, h->lut, sizeof(d.lut));
         } else {
             std::memcpy(hthr + (size_t)s * 54, h->thr, 54 * sizeof(uint64_t));
             d.bc_thr = R->d_bcthr() + (size_t)s * 54;

@@ -127,6 +127,17 @@ __device__ __forceinline__ uint32_t philox_site_w0(uint32_t site_lo, const Philo
     return __umulhi(c2, kPhiloxB) ^ c1 ^ rk.k0[9];
 }
 
+// All four output words (lookup-table random bits).
+__device__ __forceinline__ uint4 philox_site_w4(uint32_t site_lo, const PhiloxChunk& pc, const RoundKeys& rk)
+{
+    uint32_t c0, c1, c2, c3;
+    philox_site_r9(site_lo, pc, rk, c0, c1, c2, c3);
+    uint32_t h0, l0, h1, l1;
+    mul_wide(c0, kPhiloxA, h0, l0);
+    mul_wide(c2, kPhiloxB, h1, l1);
+    return make_uint4(h1 ^ c1 ^ rk.k0[9], l1, h0 ^ c3 ^ rk.k1[9], l0);
+}
+
 // Output words 0 and 1 (Blume-Capel decision and proposal).
 __device__ __forceinline__ uint2 philox_site_w01(uint32_t site_lo, const PhiloxChunk& pc, const RoundKeys& rk)
 {

@@ -90,24 +90,36 @@ struct IsingPhase {
 // colour-1 end, and a colour-1 site's four neighbours are colour 0 and
 // already final, so B = sum over colour-1 sites of s * h after the update;
 // M and Q are summed over whole words, which are final after this phase.
+// Loads, neighbour words and uphill classes of one Ising item, shared by
+// both random-number modes.
+template <int CW>
+struct IsingItem {
+    uint64_t* row;
+    uint32_t y, ch, p;
+    uint64_t amask;
+    uint64_t c[CW], flip[CW], u8[CW], u4[CW];
+    int dpre;  // disagreeing bonds of active sites after the flips decided so far
+};
+
 template <int CW, bool OBS, bool CG>
-__device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys& rk, uint64_t item, int lane,
-                                           PhaseAcc& acc)
+__device__ __forceinline__ void ising_classify(const IsingPhase& a, uint64_t item, int lane, bool modes,
+                                               IsingItem<CW>& it)
 {
     const uint32_t cpr = a.W / CW;  // chunks per row
-    const uint64_t all8 = a.mode8 == kAlwaysAccept ? ~0ull : 0ull;
-    const uint64_t all4 = a.mode4 == kAlwaysAccept ? ~0ull : 0ull;
-    const uint64_t drw8 = a.mode8 == kDraw ? ~0ull : 0ull;
-    const uint64_t drw4 = a.mode4 == kDraw ? ~0ull : 0ull;
-    const uint32_t y = (uint32_t)(item / cpr);
-    const uint32_t ch = (uint32_t)(item - (uint64_t)y * cpr);
+    const uint64_t all8 = modes && a.mode8 == kAlwaysAccept ? ~0ull : 0ull;
+    const uint64_t all4 = modes && a.mode4 == kAlwaysAccept ? ~0ull : 0ull;
+    it.y = (uint32_t)(item / cpr);
+    it.ch = (uint32_t)(item - (uint64_t)it.y * cpr);
+    const uint32_t y = it.y, ch = it.ch;
     const uint32_t yn = y == 0 ? a.L - 1 : y - 1;
     const uint32_t ys = y + 1 == a.L ? 0 : y + 1;
     uint64_t* row = a.spins + (uint64_t)y * a.W;
+    it.row = row;
     const uint64_t* rown = a.spins + (uint64_t)yn * a.W;
     const uint64_t* rows = a.spins + (uint64_t)ys * a.W;
 
-    uint64_t c[CW], n[CW], s[CW];
+    uint64_t n[CW], s[CW];
+    uint64_t* c = it.c;
     if constexpr (CW == 2) {
         const ulonglong2 vc = ld<CG>(reinterpret_cast<const ulonglong2*>(row) + ch);
         const ulonglong2 vn = ld<CG>(reinterpret_cast<const ulonglong2*>(rown) + ch);
@@ -132,10 +144,10 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
         e[0] = (c[0] >> 1) | (right << 63);
     }
 
-    const uint32_t p = (y + a.colour) & 1u;
-    const uint64_t amask = kEvenBits << p;
-    uint64_t flip[CW], u8[CW], need[CW];
-    int dpre = 0;  // disagreeing bonds of active sites after the flips decided without a draw
+    it.p = (y + a.colour) & 1u;
+    const uint64_t amask = kEvenBits << it.p;
+    it.amask = amask;
+    it.dpre = 0;
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
         const uint64_t dn = c[k] ^ n[k], ds = c[k] ^ s[k], dw = c[k] ^ w[k], de = c[k] ^ e[k];
@@ -143,21 +155,53 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
         const uint64_t x2 = dw ^ de, a2 = dw & de;
         const uint64_t eq3 = (x1 ^ x2) & ~(a1 | a2);  // exactly one neighbour differs
         const uint64_t eq4 = ~(dn | ds | dw | de);    // none differs
-        u8[k] = eq4 & amask;
-        const uint64_t u4 = eq3 & amask;
-        flip[k] = (amask & ~(eq4 | eq3)) | (u8[k] & all8) | (u4 & all4);
-        need[k] = (u8[k] & drw8) | (u4 & drw4);
+        it.u8[k] = eq4 & amask;
+        it.u4[k] = eq3 & amask;
+        it.flip[k] = (amask & ~(eq4 | eq3)) | (it.u8[k] & all8) | (it.u4[k] & all4);
         if constexpr (OBS) {
-            const uint64_t f = flip[k];
-            dpre += __popcll((dn ^ f) & amask) + __popcll((ds ^ f) & amask) + __popcll((dw ^ f) & amask) +
-                    __popcll((de ^ f) & amask);
+            const uint64_t f = it.flip[k];
+            it.dpre += __popcll((dn ^ f) & amask) + __popcll((ds ^ f) & amask) + __popcll((dw ^ f) & amask) +
+                       __popcll((de ^ f) & amask);
         }
     }
+}
+
+// Store the new words and add the fused observables.
+template <int CW, bool OBS>
+__device__ __forceinline__ void ising_finish(IsingItem<CW>& it, PhaseAcc& acc)
+{
+    uint64_t cn[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) cn[k] = it.c[k] ^ it.flip[k];
+    if constexpr (CW == 2) {
+        reinterpret_cast<ulonglong2*>(it.row)[it.ch] = make_ulonglong2(cn[0], cn[1]);
+    } else {
+        it.row[it.ch] = cn[0];
+    }
+    if constexpr (OBS) {
+        acc.B += 128 * CW - 2 * it.dpre;  // 32 active sites x 4 bonds per word
+#pragma unroll
+        for (int k = 0; k < CW; ++k) acc.M += 2 * __popcll(cn[k]) - 64;
+        acc.Q += 64 * CW;
+    }
+}
+
+template <int CW, bool OBS, bool CG>
+__device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys& rk, uint64_t item, int lane,
+                                           PhaseAcc& acc)
+{
+    IsingItem<CW> it;
+    ising_classify<CW, OBS, CG>(a, item, lane, true, it);
+    const uint64_t drw8 = a.mode8 == kDraw ? ~0ull : 0ull;
+    const uint64_t drw4 = a.mode4 == kDraw ? ~0ull : 0ull;
+    uint64_t need[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) need[k] = (it.u8[k] & drw8) | (it.u4[k] & drw4);
 
     acc.D += __popcll(need[0]) + (CW == 2 ? __popcll(need[CW - 1]) : 0);
     if (__any_sync(kFullMask, (need[0] | need[CW - 1]) != 0)) {
-        const uint64_t base = (uint64_t)y * a.L + (uint64_t)ch * (64u * CW);
-        const uint32_t site0 = (uint32_t)base + p;  // chunks never straddle 2^32 (64*CW | 2^32)
+        const uint64_t base = (uint64_t)it.y * a.L + (uint64_t)it.ch * (64u * CW);
+        const uint32_t site0 = (uint32_t)base + it.p;  // chunks never straddle 2^32 (64*CW | 2^32)
         const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
         uint32_t r4[CW][2], r8[CW][2];  // [word][32-bit half]: u < thr4, u < thr8
 #pragma unroll
@@ -165,7 +209,7 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
             uint32_t acc4[CW], acc8[CW];
 #pragma unroll
             for (int k = 0; k < CW; ++k) acc4[k] = acc8[k] = 0;
-            uint32_t bit = 1u << p;
+            uint32_t bit = 1u << it.p;
 #pragma unroll 2
             for (uint32_t j = 0; j < 16; ++j) {
                 const uint32_t off = 32u * half + 2u * j;
@@ -187,27 +231,73 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
         for (int k = 0; k < CW; ++k) {
             const uint64_t R4 = ((uint64_t)r4[k][1] << 32) | r4[k][0];
             const uint64_t R8 = ((uint64_t)r8[k][1] << 32) | r8[k][0];
-            const uint64_t acc8 = need[k] & u8[k] & R8, acc4 = need[k] & ~u8[k] & R4;
-            flip[k] |= acc8 | acc4;
+            const uint64_t acc8 = need[k] & it.u8[k] & R8, acc4 = need[k] & ~it.u8[k] & R4;
+            it.flip[k] |= acc8 | acc4;
             // an accepted 3-agree site goes from 1 to 3 disagreeing bonds, a 4-agree site from 0 to 4
-            if constexpr (OBS) dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
+            if constexpr (OBS) it.dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
         }
     }
+    ising_finish<CW, OBS>(it, acc);
+}
 
-    uint64_t cn[CW];
+// Index of the largest entry not above u in the sorted 16-entry table
+// (entry 0 is 0): a four-step binary search.
+__device__ __forceinline__ uint32_t lut_find(const uint32_t* t, uint32_t u)
+{
+    uint32_t j = u >= t[8] ? 8u : 0u;
+    j += u >= t[j + 4] ? 4u : 0u;
+    j += u >= t[j + 2] ? 2u : 0u;
+    j += u >= t[j + 1] ? 1u : 0u;
+    return j;
+}
+
+// Bit k of x to bit 2k of the result.
+__device__ __forceinline__ uint64_t spread_even(uint32_t v)
+{
+    uint64_t x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+
+// The paper's lookup-table random bits (section 3.2, LAT_RNG_TABLE): per
+// 64-bit word, four Philox blocks (counters 4w+q, sweep, colour+2) give 16
+// uniforms; each is located in the table s_lut, and the index is four
+// random bits.  Uniforms 0..7 build word e0, 8..15 word e1 (bits 4i..4i+3
+// from uniform i), whose bit k belongs to the word's k-th active site.  A
+// 3-agree site flips iff its e0 bit is set, a 4-agree site iff its e0 and
+// e1 bits are.
+template <int CW, bool OBS, bool CG>
+__device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundKeys& rk, const uint32_t* s_lut,
+                                               uint64_t item, int lane, PhaseAcc& acc)
+{
+    IsingItem<CW> it;
+    ising_classify<CW, OBS, CG>(a, item, lane, false, it);
+    acc.D += 4 * CW;
 #pragma unroll
-    for (int k = 0; k < CW; ++k) cn[k] = c[k] ^ flip[k];
-    if constexpr (CW == 2) {
-        reinterpret_cast<ulonglong2*>(row)[ch] = make_ulonglong2(cn[0], cn[1]);
-    } else {
-        row[ch] = cn[0];
-    }
-    if constexpr (OBS) {
-        acc.B += 128 * CW - 2 * dpre;  // 32 active sites x 4 bonds per word
+    for (int k = 0; k < CW; ++k) {
+        const uint64_t w = (uint64_t)it.y * a.W + (uint64_t)it.ch * CW + k;  // word index
+        const uint64_t ctr = 4ull * w;                                      // 4w+q never carries into the high word
+        const PhiloxChunk pc = philox_chunk((uint32_t)(ctr >> 32), a.sweep, a.colour + 2u, rk);
+        uint32_t e0 = 0, e1 = 0;
 #pragma unroll
-        for (int k = 0; k < CW; ++k) acc.M += 2 * __popcll(cn[k]) - 64;
-        acc.Q += 64 * CW;
+        for (int q = 0; q < 4; ++q) {
+            const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)q, pc, rk);
+            const uint32_t j0 = lut_find(s_lut, r.x), j1 = lut_find(s_lut, r.y);
+            const uint32_t j2 = lut_find(s_lut, r.z), j3 = lut_find(s_lut, r.w);
+            const uint32_t nib = j0 | (j1 << 4) | (j2 << 8) | (j3 << 12);  // uniforms 4q .. 4q+3
+            if (q < 2) e0 |= nib << (16 * q);
+            else e1 |= nib << (16 * (q - 2));
+        }
+        const uint64_t x0 = spread_even(e0) << it.p, x1 = spread_even(e1) << it.p;
+        const uint64_t acc4 = it.u4[k] & x0, acc8 = it.u8[k] & x0 & x1;
+        it.flip[k] |= acc4 | acc8;
+        if constexpr (OBS) it.dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
     }
+    ising_finish<CW, OBS>(it, acc);
 }
 
 // Three-bit sum of four one-bit words (bit-sliced): returns b0 + 2 b1 + 4 b2.

@@ -98,3 +98,18 @@ def test_thresholds_equal_the_oracle_bit_for_bit(orc):
         lib = b.lat_thresholds(p)
         ref = orc.thresholds(model, J, T, Delta)
         assert np.array_equal(lib, ref), (model, J, T, Delta)
+
+
+def test_lut_tables_equal_the_oracle_bit_for_bit(orc):
+    rng = np.random.default_rng(9)
+    temps = [b.TC_ISING, 0.9 * b.TC_ISING, 0.05, 0.3, 50.0, 1e12] + list(rng.uniform(0.5, 5.0, 40))
+    for T in temps:
+        for J in (1.0, 0.5):
+            p = b.make_params(0, 128, float(T), 1, J=J, rng=b.LAT_RNG_TABLE)
+            assert np.array_equal(b.lat_lut_table(p), orc.lut_table(J, float(T))), (J, T)
+
+
+def test_lut_mode_is_ising_only():
+    assert b.lat_footprint(b.make_params(1, 128, 1.0, 1, rng=b.LAT_RNG_TABLE)) == 0
+    assert b.lat_footprint(b.make_params(0, 128, 1.0, 1, rng=2)) == 0
+    assert b.lat_footprint(b.make_params(0, 128, 1.0, 1, rng=b.LAT_RNG_TABLE)) > 0

@@ -74,3 +74,16 @@ def test_flip_symmetry(orc):
         orc.sweep_lut(a, seed, tbl, t)
         orc.sweep_lut(b, seed, tbl, t)
         assert np.array_equal(a, -b)
+
+
+def test_strip_form_equals_full_sweep(orc):
+    L, seed, t = 128, 21, 5
+    tbl = orc.lut_table(1.0, TC)
+    s = orc.init(0, L, seed)
+    for i in range(t):
+        orc.sweep_lut(s, seed, tbl, i)
+    full = orc.sweep_lut(s.copy(), seed, tbl, t)
+    for y0, H in [(0, 8), (60, 5), (126, 4)]:
+        strip = np.ascontiguousarray(s[[(y0 - 2 + i) % L for i in range(H + 4)]])
+        orc.sweep_strip_lut(L, seed, tbl, t, y0, strip)
+        assert np.array_equal(strip[2:H + 2], full[[(y0 + i) % L for i in range(H)]])
