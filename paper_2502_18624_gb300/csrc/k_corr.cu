@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
     const int nwarps = blockDim.x >> 5;
     const uint32_t q0 = (blockIdx.y * nwarps + warp) * NQ;
     uint32_t* row = sm;
-    int acc[NQ];
+    int acc[NQ];        // Ising: carries of the carry-save sums; Blume-Capel: the sums themselves
+    uint32_t ones[NQ];  // Ising: carry-save sum bits
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) acc[k] = 0;
+    for (int k = 0; k < NQ; ++k) acc[k] = 0, ones[k] = 0;
     const uint32_t ybeg = blockIdx.x * rows_per_block;
     const uint32_t yend = min(ybeg + rows_per_block, L);
     for (uint32_t y = ybeg; y < yend; ++y) {
@@ -98,17 +99,41 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
             if constexpr (MODEL == 1) wing[k] = rot_word(row + W32, W32, j, s);
         }
         uint32_t jn = (q0 + NQ) % W32;  // (i + q0 + NQ) mod W32: the word entering the window
+        if constexpr (MODEL == 0) {
+            // Words i and i+1 (W32 is even) go through one carry-save step per
+            // distance: sum bits stay in ones[k], the carries are counted.
+            for (uint32_t ib = 0; ib < W32; ib += 2 * NQ) {
+#pragma unroll
+                for (int u = 0; u < 2 * NQ; u += 2) {
+                    const uint32_t i = ib + u;
+                    if (i < W32) {
+                        const uint32_t a1 = row[i], a2 = row[i + 1];
+                        uint32_t x1[NQ];
+#pragma unroll
+                        for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
+                        win[u % NQ] = rot_word(row, W32, jn, s);
+                        jn = jn + 1 == W32 ? 0 : jn + 1;
+#pragma unroll
+                        for (int k = 0; k < NQ; ++k) {
+                            const uint32_t x2 = a2 ^ win[(u + 1 + k) % NQ];
+                            const uint32_t t = ones[k] ^ x1[k];
+                            acc[k] += __popc((ones[k] & x1[k]) | (t & x2));
+                            ones[k] = t ^ x2;
+                        }
+                        win[(u + 1) % NQ] = rot_word(row, W32, jn, s);
+                        jn = jn + 1 == W32 ? 0 : jn + 1;
+                    }
+                }
+            }
+            continue;
+        }
         for (uint32_t ib = 0; ib < W32; ib += NQ) {
 #pragma unroll
             for (int u = 0; u < NQ; ++u) {
                 const uint32_t i = ib + u;
                 if (i < W32) {
                     const uint32_t a = row[i];
-                    if constexpr (MODEL == 0) {
-#pragma unroll
-                        for (int k = 0; k < NQ; ++k) acc[k] += __popc(a ^ win[(u + k) % NQ]);
-                        win[u] = rot_word(row, W32, jn, s);
-                    } else {
+                    {
                         const uint32_t ag = row[W32 + i];
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) {
@@ -128,7 +153,8 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
     for (int k = 0; k < NQ; ++k) {
         const uint32_t r = 32u * (q0 + k) + s;
         if (r <= rmax && rows) {
-            const long long v = MODEL == 0 ? rows * (long long)L - 2ll * acc[k] : (long long)acc[k];
+            const long long mism = 2ll * acc[k] + __popc(ones[k]);  // Ising: disagreeing pairs
+            const long long v = MODEL == 0 ? rows * (long long)L - 2ll * mism : (long long)acc[k];
             atomicAdd(reinterpret_cast<unsigned long long*>(cx + r), (unsigned long long)v);
         }
     }
@@ -137,12 +163,14 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
 // y: a block owns a 32-word column strip, a segment of rows [y0, y0+H) and
 // the distances r0 .. r0 + kYWarps*NQ - 1.  The rows y0 + r0 + t (t >= 0)
 // that row y0 + y pairs with stream through a shared-memory ring of
-// YRing<NQ>::rows rows; each step stages NQ new A rows and NQ new ring rows,
-// so the register window's slot rotation restarts at every step and stays a
-// compile-time pattern.
+// YRing<NQ>::rows rows; each step stages 2 NQ new A rows and 2 NQ new ring
+// rows, so the register window's slot rotation restarts at every step and
+// stays a compile-time pattern, and (Ising) rows y and y+1 share one
+// carry-save step per distance.
 template <int NQ>
 struct YRing {
-    static constexpr uint32_t need = (kYWarps + 1) * NQ + 1;
+    static constexpr uint32_t step = 2 * NQ;  // rows staged per step
+    static constexpr uint32_t need = kYWarps * NQ + step + 1;
     static constexpr uint32_t rows = need <= 64 ? 64 : (need <= 128 ? 128 : 256);
 };
 
@@ -178,7 +206,7 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
     const uint32_t H = min(rows_per_block, L - y0);
     const uint32_t r0 = blockIdx.z * D;
     uint32_t* ring = sm;                // R x 32 words per plane
-    uint32_t* arow = sm + R * 32 * P;   // NQ x 32 words per plane
+    uint32_t* arow = sm + R * 32 * P;   // 2 NQ x 32 words per plane
 
     // Lattice row of ring entry t is (y0 + r0 + t) mod L (staging only, so a
     // plain modulo is cheap next to the pair work).
@@ -192,21 +220,23 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
         if constexpr (P == 2) ring[R * 32 + (rr % R) * 32 + c] = vg;
     }
 
+    constexpr uint32_t S = YRing<NQ>::step;
     const uint32_t g0 = (uint32_t)warp * NQ;
-    int acc[NQ];
+    int acc[NQ];        // Ising: carries of the carry-save sums; Blume-Capel: the sums themselves
+    uint32_t ones[NQ];  // Ising: carry-save sum bits
     uint32_t win[NQ], wing[NQ];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) acc[k] = 0;
-    for (uint32_t ys = 0; ys < H; ys += NQ) {
+    for (int k = 0; k < NQ; ++k) acc[k] = 0, ones[k] = 0;
+    for (uint32_t ys = 0; ys < H; ys += S) {
         __syncthreads();  // the previous step's ring rows and A rows are no longer read
-        for (uint32_t t = threadIdx.x; t < 2 * NQ * 32; t += blockDim.x) {
-            const uint32_t rr = (t / 32) % NQ, c = t % 32;
+        for (uint32_t t = threadIdx.x; t < 2 * S * 32; t += blockDim.x) {
+            const uint32_t rr = (t / 32) % S, c = t % 32;
             uint32_t vn, vg;
-            if (t < NQ * 32) {
+            if (t < S * 32) {
                 const uint32_t ya = (uint32_t)(((uint64_t)y0 + ys + rr) % L);
                 load_strip_word<MODEL>(spins, W32, ya, j0 + c, c < tw && ys + rr < H, vn, vg);
                 arow[rr * 32 + c] = vn;
-                if constexpr (P == 2) arow[NQ * 32 + rr * 32 + c] = vg;
+                if constexpr (P == 2) arow[S * 32 + rr * 32 + c] = vg;
             } else {
                 const uint32_t tb = D + ys + rr;
                 load_strip_word<MODEL>(spins, W32, brow(tb), j0 + c, c < tw, vn, vg);
@@ -222,31 +252,50 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
             win[k] = ring[(tb % R) * 32 + lane];
             if constexpr (P == 2) wing[k] = ring[R * 32 + (tb % R) * 32 + lane];
         }
+        if constexpr (MODEL == 0) {
 #pragma unroll
-        for (int u = 0; u < NQ; ++u) {
-            if (ys + u < H) {
-                const uint32_t a = arow[u * 32 + lane];
-                if constexpr (MODEL == 0) {
+            for (int u = 0; u < (int)S; u += 2) {
+                if (ys + u < H) {
+                    const bool second = ys + u + 1 < H;
+                    const uint32_t a1 = arow[u * 32 + lane], a2 = arow[(u + 1) * 32 + lane];
+                    uint32_t x1[NQ];
 #pragma unroll
-                    for (int k = 0; k < NQ; ++k) acc[k] += __popc(a ^ win[(u + k) % NQ]);
-                } else {
-                    const uint32_t ag = arow[NQ * 32 + u * 32 + lane];
+                    for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
+                    uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
+                    win[u % NQ] = ring[(tb % R) * 32 + lane];
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) {
+                        const uint32_t x2 = second ? a2 ^ win[(u + 1 + k) % NQ] : 0u;
+                        const uint32_t t = ones[k] ^ x1[k];
+                        acc[k] += __popc((ones[k] & x1[k]) | (t & x2));
+                        ones[k] = t ^ x2;
+                    }
+                    tb += 1;
+                    win[(u + 1) % NQ] = ring[(tb % R) * 32 + lane];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < (int)S; ++u) {
+                if (ys + u < H) {
+                    const uint32_t a = arow[u * 32 + lane];
+                    const uint32_t ag = arow[S * 32 + u * 32 + lane];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
                         const uint32_t both = a & win[(u + k) % NQ];
                         acc[k] += __popc(both) - 2 * __popc(both & (ag ^ wing[(u + k) % NQ]));
                     }
+                    const uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
+                    win[u % NQ] = ring[(tb % R) * 32 + lane];
+                    wing[u % NQ] = ring[R * 32 + (tb % R) * 32 + lane];
                 }
-                const uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
-                win[u] = ring[(tb % R) * 32 + lane];
-                if constexpr (P == 2) wing[u] = ring[R * 32 + (tb % R) * 32 + lane];
             }
         }
     }
     const bool colok = (uint32_t)lane < tw;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
-        int v = colok ? acc[k] : 0;
+        int v = colok ? (MODEL == 0 ? 2 * acc[k] + __popc(ones[k]) : acc[k]) : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
         const uint32_t r = r0 + g0 + k;
@@ -286,8 +335,12 @@ cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx
     const uint32_t groups = (rmax / 32 + 1 + NQ - 1) / NQ;   // word-offset groups of NQ
     const uint32_t nwarps = groups < (uint32_t)kXWarpsMax ? groups : (uint32_t)kXWarpsMax;
     const uint32_t gy = (groups + nwarps - 1) / nwarps;
-    // rows per block: about 8 resident blocks per SM worth of work, at least 8 rows
-    const uint64_t want_blocks = (uint64_t)sms * 8 * 4 / gy + 1;
+    // rows per block: enough blocks for about eight full waves, so the last
+    // partial wave costs little; at least 8 rows per block
+    int resident = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_corr_x<MODEL, NQ>, nwarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t want_blocks = (uint64_t)sms * (resident < 1 ? 1 : resident) * 8 / gy + 1;
     uint32_t rpb = (uint32_t)((L + want_blocks - 1) / want_blocks);
     rpb = rpb < 8 ? 8 : rpb;
     // per-lane popcount sums stay below 2^31: at most L per row
@@ -302,17 +355,21 @@ template <int MODEL, int NQ>
 cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t smem = (size_t)(YRing<NQ>::rows + NQ) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
+    const size_t smem = (size_t)(YRing<NQ>::rows + YRing<NQ>::step) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_corr_y<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint32_t per_block = kYWarps * NQ;
     const uint32_t strips = (W32 + 31) / 32, chunks = (rmax + per_block) / per_block;
-    // row segments: enough blocks for about 4 per SM, segments of at least 4 steps
-    const uint64_t want = (uint64_t)sms * 4 / ((uint64_t)strips * chunks) + 1;
+    // row segments: enough blocks for about eight full waves, segments of at least two steps
+    int resident = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_corr_y<MODEL, NQ>, kYWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (uint64_t)sms * (resident < 1 ? 1 : resident) * 8 / ((uint64_t)strips * chunks) + 1;
     uint32_t rpb = (uint32_t)((L + want - 1) / want);
-    const uint32_t minrows = 4 * NQ;
+    const uint32_t step = YRing<NQ>::step;
+    const uint32_t minrows = 2 * step;
     rpb = rpb < minrows ? minrows : rpb;
-    rpb = (rpb + NQ - 1) / NQ * NQ;
+    rpb = (rpb + step - 1) / step * step;
     const dim3 grid(strips, (L + rpb - 1) / rpb, chunks);
     k_corr_y<MODEL, NQ><<<grid, kYWarps * 32, smem, st>>>(spins, L, rmax, rpb, cy);
     return cudaGetLastError();
