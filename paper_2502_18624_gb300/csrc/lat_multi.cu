@@ -45,6 +45,13 @@ namespace {
 
 constexpr int kMultiThreads = 256;
 constexpr uint32_t kDefaultTile = 4096;  // items per tile when no schedule entry applies
+constexpr uint32_t kTilesPerBlock = 4;   // a phase with few lattices left still has this many tiles per block
+
+uint32_t items_of(const lat* h)
+{
+    const uint32_t cw = (h->p.model == LAT_ISING && h->W % 2 == 0) ? 2 : 1;
+    return (uint32_t)((uint64_t)h->p.L * (h->p.model == LAT_ISING ? h->W / cw : h->W));
+}
 
 struct MultiDesc {
     void* spins;
@@ -267,7 +274,8 @@ size_t host_bytes_for(uint32_t cap, uint32_t max_sweeps)
 {
     return (size_t)cap * sizeof(MultiDesc) + ((size_t)cap + 1) * sizeof(uint32_t) +
            (2 * (size_t)max_sweeps + 1) * sizeof(unsigned long long) + 2 * (size_t)max_sweeps * sizeof(uint32_t) +
-           sizeof(MultiCtl) + (size_t)cap * 54 * sizeof(unsigned long long) + 64;
+           sizeof(MultiCtl) + (size_t)cap * 54 * sizeof(unsigned long long) + 64 + 256 +
+           (size_t)cap * max_sweeps * kObsWords * sizeof(long long);
 }
 
 cudaError_t enqueue_run(lat_runner* R, cudaStream_t st, uint32_t n)
@@ -420,7 +428,24 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     MultiCtl* hctl = reinterpret_cast<MultiCtl*>(hp);
     hp += sizeof(MultiCtl);
     unsigned long long* hthr = reinterpret_cast<unsigned long long*>(hp);
+    hp += (size_t)R->cap * 54 * sizeof(unsigned long long);
+    long long* hobs = reinterpret_cast<long long*>(R->host + (((size_t)(hp - R->host) + 255) / 256 * 256));
 
+    // The sparsest phase of lattice order[s] is its last one, where only the
+    // lattices with at least as many sweeps are active: their items are
+    // busy[s].  A tile of that lattice is capped at busy[s] / (kTilesPerBlock *
+    // grid), so that a lattice left almost alone at the end of a run still
+    // spreads over every block (a schedule tuned for a full batch would not).
+    std::vector<uint64_t> busy(n);
+    {
+        uint64_t acc = 0;
+        uint32_t s = 0;
+        while (s < n) {
+            uint32_t e2 = s;
+            while (e2 < n && nsweeps[order[e2]] == nsweeps[order[s]]) acc += items_of(lattices[order[e2++]]);
+            for (; s < e2; ++s) busy[s] = acc;
+        }
+    }
     uint32_t maxs = 0;
     uint64_t tiles_acc = 0;
     for (uint32_t s = 0; s < n; ++s) {
@@ -434,9 +459,11 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
         d.L = h->p.L;
         d.W = h->W;
         d.cw = (h->p.model == LAT_ISING && h->W % 2 == 0) ? 2 : 1;
-        d.items = (uint32_t)((uint64_t)h->p.L * (h->p.model == LAT_ISING ? h->W / d.cw : h->W));
+        d.items = items_of(h);
         auto it = R->tile_of.find({h->p.model, h->p.L});
         uint32_t tile = it != R->tile_of.end() ? it->second : kDefaultTile;
+        const uint64_t cap = busy[s] / ((uint64_t)kTilesPerBlock * (uint64_t)R->grid) / kMultiThreads * kMultiThreads;
+        if (tile > cap) tile = (uint32_t)std::max<uint64_t>(cap, kMultiThreads);
         if (tile > d.items) tile = (d.items + kMultiThreads - 1) / kMultiThreads * kMultiThreads;
         d.tile_items = tile;
         d.ntiles = (d.items + tile - 1) / tile;
@@ -488,30 +515,23 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     up(R->lay.active, hact, (size_t)K * sizeof(uint32_t));
     up(R->lay.ctl, hctl, sizeof(MultiCtl));
     up(R->lay.bcthr, hthr, (size_t)n * 54 * sizeof(unsigned long long));
-    // per-sweep records of the lattices in this run start at zero
-    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
-        if (nsweeps[i])
-            e = cudaMemsetAsync(R->d_obs() + (size_t)i * R->max_sweeps * kObsWords, 0,
-                                (size_t)nsweeps[i] * kObsWords * sizeof(long long), st);
+    // per-sweep records of the lattices in this run start at zero (one contiguous region)
+    const size_t obs_words = (size_t)n * R->max_sweeps * kObsWords;
+    if (e == cudaSuccess && maxs > 0) e = cudaMemsetAsync(R->d_obs(), 0, obs_words * sizeof(long long), st);
     if (e == cudaSuccess && K > 0) e = R->have_graph ? cudaGraphLaunch(R->graph, st) : enqueue_run(R, st, n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hctl, R->d_ctl(), sizeof(MultiCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return LAT_ECUDA;
     if (hctl->error) return LAT_ETIMEDOUT;
 
-    if (per_sweep) {
-        std::vector<size_t> at(n + 1, 0);
-        for (uint32_t i = 0; i < n; ++i) at[i + 1] = at[i] + (per_sweep[i] ? (size_t)nsweeps[i] * kObsWords : 0);
-        std::vector<long long> rec(at[n]);
-        for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
-            if (at[i + 1] > at[i])
-                e = cudaMemcpyAsync(rec.data() + at[i], R->d_obs() + (size_t)i * R->max_sweeps * kObsWords,
-                                    (at[i + 1] - at[i]) * sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (per_sweep && maxs > 0) {
+        // one copy of the whole record region into pinned staging
+        e = cudaMemcpyAsync(hobs, R->d_obs(), obs_words * sizeof(long long), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return LAT_ECUDA;
         for (uint32_t i = 0; i < n; ++i) {
-            if (at[i + 1] == at[i]) continue;
-            const long long* r = rec.data() + at[i];
+            if (!per_sweep[i] || nsweeps[i] == 0) continue;
+            const long long* r = hobs + (size_t)i * R->max_sweeps * kObsWords;
             for (uint32_t s = 0; s < nsweeps[i]; ++s) {
                 lat_obs& o = per_sweep[i][s];
                 o.M = r[(size_t)s * kObsWords + kObsM];
