@@ -54,6 +54,10 @@ def _bind(lib):
         "or_sweep_strip": (None, [i32, u32, u64, P, u32, u64, u32, P]),
         "or_measure": (None, [i32, u32, P, P]),
         "or_correlation": (None, [u32, P, u32, P, P]),
+        "or_protocol_rc": (u64, [u32, u64]),
+        "or_protocol_distances": (u32, [u32, u64, u32, P, u32]),
+        "or_protocol_times": (u32, [u64, P, u32]),
+        "or_correlation_sampled": (None, [u32, P, u32, P, u32, P, P]),
         "or_sd_hist": (None, [u32, P, P]),
         "or_pack": (None, [i32, u32, P, P]),
         "or_hash_words": (u64, [P, u64]),
@@ -172,6 +176,36 @@ def correlation(s: np.ndarray, rmax: int) -> tuple[np.ndarray, np.ndarray]:
     cx = np.zeros(rmax + 1, dtype=np.int64)
     cy = np.zeros(rmax + 1, dtype=np.int64)
     _load().or_correlation(s.shape[0], _p(np.ascontiguousarray(s)), rmax, _p(cx), _p(cy))
+    return cx, cy
+
+
+def protocol_rc(L: int, t: int) -> int:
+    """r_c(t) of the section 3.3 protocol."""
+    return int(_load().or_protocol_rc(L, t))
+
+
+def protocol_distances(L: int, t: int, R: int = 16) -> np.ndarray:
+    """Distances measured from the downsampled sources at time t (uint32, ascending)."""
+    n = int(_load().or_protocol_distances(L, t, R, None, 0))
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    _load().or_protocol_distances(L, t, R, _p(out), n)
+    return out[:n]
+
+
+def protocol_times(tmax: int) -> np.ndarray:
+    """Measurement times floor(2^(x/8) + 0.5) <= tmax (uint64, ascending, distinct)."""
+    n = int(_load().or_protocol_times(tmax, None, 0))
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    _load().or_protocol_times(tmax, _p(out), n)
+    return out[:n]
+
+
+def correlation_sampled(s: np.ndarray, R: int, r) -> tuple[np.ndarray, np.ndarray]:
+    """Sums over one source per R x R square (top-left corner) for each r in the list."""
+    rr = np.ascontiguousarray(np.asarray(r, dtype=np.uint32).reshape(-1))
+    cx = np.zeros(rr.size, dtype=np.int64)
+    cy = np.zeros(rr.size, dtype=np.int64)
+    _load().or_correlation_sampled(s.shape[0], _p(np.ascontiguousarray(s)), R, _p(rr), rr.size, _p(cx), _p(cy))
     return cx, cy
 
 

@@ -29,6 +29,12 @@
  *                      bond identity B = Cx(1) + Cy(1).
  *   or_sd_hist         Eq. (3) equals 1 exactly under the enumerated
  *                      Boltzmann weights.
+ *   or_protocol_*      the integers the section 3.3 formulas give when
+ *                      evaluated in 60-digit decimal arithmetic, and the
+ *                      structure of the distance and time sets
+ *                      (tests/test_oracle_protocol.py).
+ *   or_correlation_sampled  equals or_correlation at R = 1; numpy array
+ *                      form (strided sources, rolled targets).
  *   or_lut_table       80-digit closed form of the cumulative pattern
  *                      probabilities (tests/test_oracle_lut.py).
  *   or_sweep_lut       Kaufman's exact finite-torus energy and Onsager's
@@ -423,6 +429,89 @@ void or_correlation(uint32_t L, const int8_t* s, uint32_t rmax, int64_t* cx, int
             }
         cx[r] = ax;
         cy[r] = ay;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The correlation protocol of section 3.3.                                   */
+/*   R = 16; every site is a source for r <= 2R; beyond that the sources are  */
+/*   one site per R x R square (its top-left corner, x % R == 0 and           */
+/*   y % R == 0), for every r up to r_c(t) and then for the log-spaced        */
+/*   distances floor(2^(x/32)) up to L/2.                                     */
+/*   r_c(t) = max{256, floor(g(L) sqrt(t) + 0.5)},                            */
+/*   g(L)   = 6 sqrt(ln(L / 2^16) / 3.3^2 + 1)   (natural logarithm).         */
+/*   Measurement times: t = floor(2^(x/8) + 0.5), x = 1, 2, ...               */
+/* All of it is computed in FP64, in the order the formulas are written.      */
+/* ------------------------------------------------------------------------ */
+uint64_t or_protocol_rc(uint32_t L, uint64_t t)
+{
+    const double g = 6.0 * sqrt(log((double)L / 65536.0) / (3.3 * 3.3) + 1.0);
+    const double v = floor(g * sqrt((double)t) + 0.5);
+    return v > 256.0 ? (uint64_t)v : 256u;
+}
+
+/* The distances measured from the downsampled sources at time t, ascending: */
+/* every r with 2R < r <= min(r_c, L/2), then every distinct floor(2^(x/32)) */
+/* with r_c < floor(2^(x/32)), for x up to 32 (log2(L) - 1) (i.e. r <= L/2). */
+/* Returns the count; writes at most cap values.                             */
+uint32_t or_protocol_distances(uint32_t L, uint64_t t, uint32_t R, uint32_t* out, uint32_t cap)
+{
+    const uint64_t rc = or_protocol_rc(L, t);
+    const uint64_t half = L / 2;
+    const uint64_t dense_end = rc < half ? rc : half;
+    uint32_t n = 0;
+    for (uint64_t r = 2 * (uint64_t)R + 1; r <= dense_end; ++r) {
+        if (n < cap) out[n] = (uint32_t)r;
+        ++n;
+    }
+    uint64_t last = dense_end;
+    for (uint32_t x = 1;; ++x) {
+        const double v = floor(exp2((double)x / 32.0));
+        if (v > (double)half) break;
+        const uint64_t r = (uint64_t)v;
+        if (r <= rc || r <= last) continue;
+        if (n < cap) out[n] = (uint32_t)r;
+        ++n;
+        last = r;
+    }
+    return n;
+}
+
+/* Distinct measurement times floor(2^(x/8) + 0.5) <= tmax, x = 1, 2, ...,   */
+/* ascending.  Returns the count; writes at most cap values.                 */
+uint32_t or_protocol_times(uint64_t tmax, uint64_t* out, uint32_t cap)
+{
+    uint32_t n = 0;
+    uint64_t last = 0;
+    for (uint32_t x = 1;; ++x) {
+        const double v = floor(exp2((double)x / 8.0) + 0.5);
+        if (v > (double)tmax) break;
+        const uint64_t t = (uint64_t)v;
+        if (t == last) continue;
+        if (n < cap) out[n] = t;
+        ++n;
+        last = t;
+    }
+    return n;
+}
+
+/* Correlation from the downsampled sources (one per R x R square, the       */
+/* top-left corner): for each listed r,                                      */
+/* cx = sum over x % R == 0, y % R == 0 of s(x,y) s(x+r,y), cy likewise with */
+/* s(x,y+r); periodic, raw int64 sums over (L/R)^2 sources.                  */
+void or_correlation_sampled(uint32_t L, const int8_t* s, uint32_t R, const uint32_t* r, uint32_t nr,
+                            int64_t* cx, int64_t* cy)
+{
+    for (uint32_t i = 0; i < nr; ++i) {
+        int64_t ax = 0, ay = 0;
+        for (uint64_t y = 0; y < L; y += R)
+            for (uint64_t x = 0; x < L; x += R) {
+                int v = s[y * L + x];
+                ax += v * s[y * L + (x + r[i]) % L];
+                ay += v * s[((y + r[i]) % L) * L + x];
+            }
+        cx[i] = ax;
+        cy[i] = ay;
     }
 }
 

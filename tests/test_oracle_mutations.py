@@ -100,6 +100,30 @@ def _lut_table_fails(orc):
     return abs(int(tbl[1]) - int(mpmath.floor(mpmath.ldexp(cum, 32)))) > 1 or int(tbl[0]) != 0
 
 
+def _rc_fails(orc):
+    import test_oracle_protocol as tp
+    return any(orc.protocol_rc(L, t) != tp._exact_rc(L, t) for L in (1 << 17, 1 << 20, 4096) for t in (10**5, 10**7))
+
+
+def _distances_fails(orc):
+    import test_oracle_protocol as tp
+    return orc.protocol_distances(1 << 17, 1000, 16).tolist() != tp._exact_distances(1 << 17, 1000, 16)
+
+
+def _times_fails(orc):
+    import test_oracle_protocol as tp
+    return orc.protocol_times(1 << 20).tolist() != tp._exact_times(1 << 20)
+
+
+def _sampled_fails(orc):
+    import test_oracle_protocol as tp
+    s = np.where(np.random.default_rng(4).random((64, 64)) < 0.5, -1, 1).astype(np.int8)
+    rs = [0, 1, 7, 33]
+    got = orc.correlation_sampled(s, 16, rs)
+    ref = tp._numpy_sampled(s, 16, rs)
+    return not (np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]))
+
+
 MUTATIONS = [
     ("sweep drops the east neighbour",
      "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
@@ -132,6 +156,16 @@ MUTATIONS = [
     ("Blume-Capel quench not uniform over three values",
      "s[site] = (int8_t)((int)(((uint64_t)w[0] * 3u) >> 32) - 1);",
      "s[site] = (int8_t)((int)(((uint64_t)w[0] * 2u) >> 32) - 1);", _init_fails),
+    ("r_c with a base-2 logarithm in g(L)", "sqrt(log((double)L / 65536.0)", "sqrt(log2((double)L / 65536.0)",
+     _rc_fails),
+    ("log-spaced distances at 16 per octave", "floor(exp2((double)x / 32.0))", "floor(exp2((double)x / 16.0))",
+     _distances_fails),
+    ("measurement times rounded down", "floor(exp2((double)x / 8.0) + 0.5)", "floor(exp2((double)x / 8.0))",
+     _times_fails),
+    ("downsampled sources on every column",
+     "            for (uint64_t x = 0; x < L; x += R) {\n                int v = s[y * L + x];\n                ax += v * s[y * L + (x + r[i]) % L];",
+     "            for (uint64_t x = 0; x < L; x += 1) {\n                int v = s[y * L + x];\n                ax += v * s[y * L + (x + r[i]) % L];",
+     _sampled_fails),
 ]
 
 
