@@ -108,8 +108,10 @@ typedef struct {
 } lat_obs;
 
 /* Device bytes lat_create needs for these parameters: the packed lattice
- * (L*L/8 bytes Ising, L*L/4 bytes Blume-Capel) plus a small workspace for
- * per-sweep observables, correlation sums and a transfer stage.
+ * (L*L/8 bytes Ising, L*L/4 bytes Blume-Capel) plus a workspace for
+ * per-sweep observables, correlation sums, a transfer stage and the compact
+ * copy of the source columns used by lat_correlation_sampled (1/16 of the
+ * lattice).
  * Returns 0 if the parameters are invalid.  Host only; needs no GPU. */
 size_t lat_footprint(const lat_params* p);
 
@@ -163,6 +165,58 @@ int lat_measure(lat_t* h, lat_obs* out);
  * raw sums (no mean subtracted, no normalisation).  cx and cy are host
  * arrays of rmax+1 entries.  rmax must be <= L/2 (LAT_EINVAL).  Synchronises. */
 int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy);
+
+/* The correlation protocol of section 3.3.  Every site is a source for
+ * r <= 2R.  Beyond that, only one site per R x R square is a source (its
+ * top-left corner, x % R == 0 and y % R == 0), and the distances are:
+ *   - every r in (2R, r_c(t)];
+ *   - the log-spaced floor(2^(x/32)) > r_c(t), 32 per octave, up to L/2;
+ * with r_c(t) = max{256, floor(g(L) sqrt(t) + 1/2)} and
+ * g(L) = 6 sqrt(ln(L / 2^16) / 3.3^2 + 1), natural logarithm.
+ * Measurements are taken at the times t = floor(2^(x/8) + 1/2), x = 1, 2, ...
+ * The formulas are evaluated on the host in FP64, in the order written and
+ * without floating-point contraction.  The functions below need no device. */
+
+/* r_c(t) for a lattice of side L. */
+uint64_t lat_protocol_rc(uint32_t L, uint64_t t);
+
+/* The downsampled distances at time t, ascending and distinct: every r in
+ * (2R, min(r_c, L/2)], then every floor(2^(x/32)) in (r_c, L/2].  Returns
+ * their number and writes the first min(number, cap) to out (which may be
+ * NULL when cap is 0). */
+uint32_t lat_protocol_distances(uint32_t L, uint64_t t, uint32_t R, uint32_t* out, uint32_t cap);
+
+/* The distinct measurement times floor(2^(x/8) + 1/2) <= tmax, ascending.
+ * Returns their number and writes the first min(number, cap) to out. */
+uint32_t lat_protocol_times(uint64_t tmax, uint64_t* out, uint32_t cap);
+
+/* Correlation from downsampled sources, for an arbitrary list of distances:
+ *   cx[i] = sum over x % R == 0, y % R == 0 of s(x,y) s(x + r[i], y),
+ *   cy[i] = the same with s(x, y + r[i]);
+ * periodic, exact int64 raw sums over (L/R)^2 sources.
+ *   R          a power of two, 1..64 (the paper uses 16).
+ *   r, nr      host array of nr distances, each <= L/2.  Repeats and any
+ *              order are allowed; lists longer than L/2 + 1 are processed
+ *              in pieces of that size.
+ *   cx, cy     host arrays of nr entries.
+ * With R >= 16, the y sums read a compact copy of the source columns that
+ * the handle's buffer holds: L/16 bits per row and plane, counted in
+ * lat_footprint.  With R < 16 they read the lattice directly.
+ * Errors: LAT_EINVAL (R not a power of two in 1..64, a distance > L/2,
+ * a NULL array with nr > 0), LAT_ECUDA.  Synchronises. */
+int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr, int64_t* cx, int64_t* cy);
+
+/* One protocol measurement at time t.  Output rows are in ascending r:
+ *   - rows 0..min(2R, L/2) hold every distance from every site
+ *     (nsrc = L^2, as lat_correlation);
+ *   - the remaining rows hold lat_protocol_distances(L, t, R) from the
+ *     downsampled sources (nsrc = (L/R)^2, as lat_correlation_sampled).
+ * *n_out always receives the row count.  A call with cap == 0 and every
+ * array NULL only queries that count and returns LAT_OK.  Otherwise all
+ * four arrays are needed, each of cap >= *n_out entries (LAT_EINVAL if
+ * fewer).  The host divides cx and cy by nsrc to normalise.  Synchronises. */
+int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uint32_t* n_out, uint32_t* r_out,
+                             int64_t* cx, int64_t* cy, uint64_t* nsrc);
 
 /* Schwinger-Dyson histogram of Eq. (3): hist[v+4] = number of sites with
  * s_x * h_x = v, v = -4..4, h_x the sum of the four neighbours.  Eq. (3)'s

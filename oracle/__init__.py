@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -88,7 +88,7 @@ def compile_variant(source_text: str, out_dir: str) -> str:
     lib = os.path.join(out_dir, "liboracle_variant.so")
     with open(src, "w") as f:
         f.write(source_text)
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", src, "-o", lib, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", src, "-o", lib, "-lm"])
     return lib
 
 

@@ -70,6 +70,11 @@ def load(build_if_missing: bool = True):
         "lat_sweep": (i32, [P, u32, P]),
         "lat_measure": (i32, [P, P]),
         "lat_correlation": (i32, [P, u32, P, P]),
+        "lat_protocol_rc": (u64, [u32, u64]),
+        "lat_protocol_distances": (u32, [u32, u64, u32, P, u32]),
+        "lat_protocol_times": (u32, [u64, P, u32]),
+        "lat_correlation_sampled": (i32, [P, u32, P, u32, P, P]),
+        "lat_correlation_protocol": (i32, [P, u64, u32, u32, P, P, P, P, P]),
         "lat_sd_hist": (i32, [P, P]),
         "lat_hash": (i32, [P, P]),
         "lat_get_spins": (i32, [P, P]),
@@ -164,6 +169,48 @@ def lat_correlation(h, rmax: int) -> tuple[np.ndarray, np.ndarray]:
     return cx, cy
 
 
+def lat_protocol_rc(L: int, t: int) -> int:
+    return int(load().lat_protocol_rc(L, t))
+
+
+def lat_protocol_distances(L: int, t: int, R: int = 16) -> np.ndarray:
+    n = int(load().lat_protocol_distances(L, t, R, None, 0))
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    load().lat_protocol_distances(L, t, R, _ptr(out), n)
+    return out[:n]
+
+
+def lat_protocol_times(tmax: int) -> np.ndarray:
+    n = int(load().lat_protocol_times(tmax, None, 0))
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    load().lat_protocol_times(tmax, _ptr(out), n)
+    return out[:n]
+
+
+def lat_correlation_sampled(h, R: int, r) -> tuple[np.ndarray, np.ndarray]:
+    rr = np.ascontiguousarray(np.asarray(r, dtype=np.uint32).reshape(-1))
+    cx = np.zeros(max(rr.size, 1), dtype=np.int64)
+    cy = np.zeros(max(rr.size, 1), dtype=np.int64)
+    _check(load().lat_correlation_sampled(h, R, _ptr(rr) if rr.size else None, rr.size, _ptr(cx), _ptr(cy)),
+           "lat_correlation_sampled")
+    return cx[:rr.size], cy[:rr.size]
+
+
+def lat_correlation_protocol(h, t: int, R: int = 16) -> dict:
+    """One section 3.3 measurement: {"r", "cx", "cy", "nsrc"} rows in ascending r."""
+    n = ctypes.c_uint32(0)
+    _check(load().lat_correlation_protocol(h, t, R, 0, ctypes.byref(n), None, None, None, None),
+           "lat_correlation_protocol")
+    k = n.value
+    r = np.zeros(k, dtype=np.uint32)
+    cx = np.zeros(k, dtype=np.int64)
+    cy = np.zeros(k, dtype=np.int64)
+    ns = np.zeros(k, dtype=np.uint64)
+    _check(load().lat_correlation_protocol(h, t, R, k, ctypes.byref(n), _ptr(r), _ptr(cx), _ptr(cy), _ptr(ns)),
+           "lat_correlation_protocol")
+    return {"r": r, "cx": cx, "cy": cy, "nsrc": ns}
+
+
 def lat_sd_hist(h) -> np.ndarray:
     out = np.zeros(9, dtype=np.int64)
     _check(load().lat_sd_hist(h, _ptr(out)), "lat_sd_hist")
@@ -251,6 +298,12 @@ class Lattice:
 
     def correlation(self, rmax: int):
         return lat_correlation(self.handle, rmax)
+
+    def correlation_sampled(self, R: int, r):
+        return lat_correlation_sampled(self.handle, R, r)
+
+    def correlation_protocol(self, t: int, R: int = 16) -> dict:
+        return lat_correlation_protocol(self.handle, t, R)
 
     def sd_hist(self):
         return lat_sd_hist(self.handle)

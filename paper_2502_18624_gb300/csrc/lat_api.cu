@@ -63,6 +63,10 @@ Layout layout_of(const lat_params* p)
     l.stage_bytes = lsq < kStageCap ? lsq : (kStageCap / p->L) * p->L;
     l.stage = off;
     off = align_up(off + l.stage_bytes);
+    l.ds = off;
+    off = align_up(off + ds_scratch_words(p->model, p->L) * sizeof(uint64_t));
+    l.rlist = off;
+    off = align_up(off + ((size_t)p->L / 2 + 1) * sizeof(uint32_t));
     l.total = off;
     return l;
 }
@@ -113,9 +117,54 @@ void build_lut(const lat_params* p, uint32_t* out)
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
 
+// Section 3.3: r_c(t) = max{256, floor(g(L) sqrt(t) + 1/2)} with
+// g(L) = 6 sqrt(ln(L / 2^16) / 3.3^2 + 1), evaluated in FP64 in that order
+// (the library is compiled without floating-point contraction).
+uint64_t protocol_rc(uint32_t L, uint64_t t)
+{
+    const double g = 6.0 * std::sqrt(std::log((double)L / 65536.0) / (3.3 * 3.3) + 1.0);
+    const double v = std::floor(g * std::sqrt((double)t) + 0.5);
+    return v > 256.0 ? (uint64_t)v : 256u;
+}
+
+bool valid_R(uint32_t R) { return R >= 1 && R <= 64 && (R & (R - 1)) == 0; }
+
 }  // namespace
 
 extern "C" {
+
+uint64_t lat_protocol_rc(uint32_t L, uint64_t t) { return protocol_rc(L, t); }
+
+uint32_t lat_protocol_distances(uint32_t L, uint64_t t, uint32_t R, uint32_t* out, uint32_t cap)
+{
+    const uint64_t rc = protocol_rc(L, t), half = L / 2;
+    std::vector<uint32_t> d;
+    // every distance in (2R, min(r_c, L/2)]
+    for (uint64_t r = 2 * (uint64_t)R + 1; r <= std::min(rc, half); ++r) d.push_back((uint32_t)r);
+    // floor(2^(x/32)) beyond r_c, 32 per octave, up to 2^(log2(L) - 1) = L/2
+    for (uint32_t x = 1; std::floor(std::exp2(x / 32.0)) <= (double)half; ++x) {
+        const uint64_t r = (uint64_t)std::floor(std::exp2(x / 32.0));
+        if (r > rc && (d.empty() || r > d.back())) d.push_back((uint32_t)r);
+    }
+    if (out)
+        for (size_t i = 0; i < d.size() && i < cap; ++i) out[i] = d[i];
+    return (uint32_t)d.size();
+}
+
+uint32_t lat_protocol_times(uint64_t tmax, uint64_t* out, uint32_t cap)
+{
+    uint32_t n = 0;
+    uint64_t prev = 0;
+    for (uint32_t x = 1;; ++x) {
+        const double v = std::floor(std::exp2(x / 8.0) + 0.5);
+        if (v > (double)tmax) break;
+        if ((uint64_t)v == prev) continue;
+        prev = (uint64_t)v;
+        if (out && n < cap) out[n] = prev;
+        ++n;
+    }
+    return n;
+}
 
 size_t lat_footprint(const lat_params* p) { return params_ok(p) ? layout_of(p).total : 0; }
 
@@ -286,6 +335,55 @@ int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy)
         e = cudaMemcpyAsync(cy, dcy, (rmax + 1) * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return cuda_err(e);
+}
+
+int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr, int64_t* cx, int64_t* cy)
+{
+    if (!h || !valid_R(R) || (nr && (!r || !cx || !cy))) return LAT_EINVAL;
+    for (uint32_t i = 0; i < nr; ++i)
+        if (r[i] > h->p.L / 2) return LAT_EINVAL;
+    // the device list and accumulators hold L/2 + 1 distances: longer lists go in pieces
+    const uint32_t piece = h->p.L / 2 + 1;
+    long long* dcx = h->corr();
+    long long* dcy = dcx + piece;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t i0 = 0; i0 < nr && e == cudaSuccess; i0 += piece) {
+        const uint32_t n = std::min(piece, nr - i0);
+        e = cudaMemcpyAsync(h->rlist(), r + i0, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = launch_correlation_sampled(h->p.model, h->spins(), h->p.L, h->W, R, h->rlist(), n, dcx, dcy,
+                                           h->ds_scratch(), h->ls.sms, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cx + i0, dcx, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cy + i0, dcy, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+        // the list and accumulators are reused by the next piece; r is read before return
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    return cuda_err(e);
+}
+
+int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uint32_t* n_out, uint32_t* r_out,
+                             int64_t* cx, int64_t* cy, uint64_t* nsrc)
+{
+    if (!h || !n_out || !valid_R(R)) return LAT_EINVAL;
+    const uint32_t L = h->p.L;
+    const uint32_t rfull = std::min<uint32_t>(2 * R, L / 2);
+    const uint32_t nds = lat_protocol_distances(L, t, R, nullptr, 0);
+    const uint32_t n = rfull + 1 + nds;
+    *n_out = n;
+    if (cap < n) return cap == 0 && !r_out && !cx && !cy && !nsrc ? LAT_OK : LAT_EINVAL;
+    if (!r_out || !cx || !cy || !nsrc) return LAT_EINVAL;
+    int rc = lat_correlation(h, rfull, cx, cy);
+    if (rc != LAT_OK) return rc;
+    const uint64_t all = (uint64_t)L * L, sampled = (uint64_t)(L / R) * (L / R);
+    for (uint32_t r = 0; r <= rfull; ++r) {
+        r_out[r] = r;
+        nsrc[r] = all;
+    }
+    lat_protocol_distances(L, t, R, r_out + rfull + 1, nds);
+    for (uint32_t i = rfull + 1; i < n; ++i) nsrc[i] = sampled;
+    return lat_correlation_sampled(h, R, r_out + rfull + 1, nds, cx + rfull + 1, cy + rfull + 1);
 }
 
 int lat_sd_hist(lat_t* h, int64_t* hist)

@@ -9,7 +9,7 @@
 #include "lat_internal.cuh"
 
 struct Layout {
-    size_t spins, obs, corr, misc, stage, total, stage_bytes;
+    size_t spins, obs, corr, misc, stage, ds, rlist, total, stage_bytes;
 };
 
 struct lat {
@@ -32,5 +32,7 @@ struct lat {
     long long* corr() const { return reinterpret_cast<long long*>(buf + lay.corr); }
     long long* misc() const { return reinterpret_cast<long long*>(buf + lay.misc); }
     int8_t* stage() const { return reinterpret_cast<int8_t*>(buf + lay.stage); }
+    uint64_t* ds_scratch() const { return reinterpret_cast<uint64_t*>(buf + lay.ds); }
+    uint32_t* rlist() const { return reinterpret_cast<uint32_t*>(buf + lay.rlist); }
 };
 

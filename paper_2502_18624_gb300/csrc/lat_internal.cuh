@@ -76,5 +76,14 @@ cudaError_t launch_pack_rows(int model, void* spins, uint32_t L, uint32_t W, uin
 // Correlation (k_corr.cu).
 cudaError_t launch_correlation(int model, const void* spins, uint32_t L, uint32_t W, uint32_t rmax,
                                long long* cx, long long* cy, cudaStream_t st);
+// Correlation from downsampled sources (k_corr_ds.cu): one source per R x R
+// square, for a list of nr distances.  R >= kDsMinScratchR uses the compact
+// source-column copy in escratch (ds_scratch_words(model, L) words).
+constexpr uint32_t kDsChunk = 2048;       // distances per launch
+constexpr uint32_t kDsMinScratchR = 16;
+size_t ds_scratch_words(int model, uint32_t L);
+cudaError_t launch_correlation_sampled(int model, const void* spins, uint32_t L, uint32_t W, uint32_t R,
+                                       const uint32_t* rlist, uint32_t nr, long long* cx, long long* cy,
+                                       uint64_t* escratch, int sms, cudaStream_t st);
 
 }  // namespace latk

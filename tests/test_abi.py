@@ -67,7 +67,22 @@ def test_footprint_covers_the_packed_lattice():
         p = b.make_params(model, L, 1.0, 1)
         state = b.lat_state_bytes(p)
         assert state == L * L // (8 if model == 0 else 4)
-        assert state <= b.lat_footprint(p) <= state + (6 << 20) + 16 * L
+        # + a 1/16 copy of the source columns (downsampled correlation) and small buffers
+        assert state <= b.lat_footprint(p) <= state + state // 16 + (6 << 20) + 40 * L
+
+
+def test_protocol_host_functions_equal_the_oracle(orc):
+    """r_c(t), the downsampled distances and the measurement times: library
+    (host C++) and oracle (C) compute them separately, in FP64, and must give
+    the same integers."""
+    for L in (64, 256, 1024, 3 << 10, 1 << 16, 1 << 17, 1 << 19, 1 << 20):
+        for t in list(range(1, 400)) + [1000, 1850, 10**5, 524288, 10**7, 10**9]:
+            assert b.lat_protocol_rc(L, t) == orc.protocol_rc(L, t)
+        for t in (1, 1000, 10**5, 10**7):
+            for R in (1, 16, 64):
+                assert np.array_equal(b.lat_protocol_distances(L, t, R), orc.protocol_distances(L, t, R)), (L, t, R)
+    for tmax in (1, 13, 1000, 1 << 20, 1 << 40):
+        assert np.array_equal(b.lat_protocol_times(tmax), orc.protocol_times(tmax))
 
 
 def test_device_calls_fail_loudly_without_a_gpu():
