@@ -306,6 +306,114 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
     }
 }
 
+// Near distances, r <= kNear = 32, both axes in one kernel (the all-sites
+// part of the section 3.3 protocol asks for r <= 2R = 32).  A block owns a
+// strip of 32 column words and kNearRows rows; it stages those rows, the
+// kNear rows below them and the word right of the strip in shared memory.
+// Warps 0..3 take the x distances 8k+1 .. 8k+8 (k = warp), warps 4..7 the y
+// distances 8k+1 .. 8k+8 (k = warp - 4); every warp walks all rows of the
+// block, lane = column word, and rows u and u+1 share one carry-save step per
+// distance.  Distance 0 is counted by warp 0 (Ising: every site; Blume-Capel:
+// the non-zero sites).
+constexpr uint32_t kNear = 32;
+constexpr uint32_t kNearRows = 64;
+constexpr uint32_t kNearStride = 33;  // 32 strip words + the next word
+
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_corr_near(const void* spins, uint32_t L, uint32_t rmax, long long* cx,
+                                                   long long* cy)
+{
+    constexpr int P = Planes<MODEL>::n;
+    constexpr uint32_t NR = kNearRows + kNear;  // staged rows
+    __shared__ uint32_t S[P][NR][kNearStride];
+    const uint32_t W32 = L / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t j0 = blockIdx.x * 32;
+    const uint32_t tw = min(32u, W32 - j0);
+    const uint32_t y0 = blockIdx.y * kNearRows;
+    for (uint32_t t = threadIdx.x; t < NR * kNearStride; t += blockDim.x) {
+        const uint32_t rr = t / kNearStride, c = t % kNearStride;
+        const uint64_t y = ((uint64_t)y0 + rr) % L;
+        uint32_t vn, vg;
+        load_strip_word<MODEL>(spins, W32, y, (j0 + c) % W32, c <= tw, vn, vg);
+        S[0][rr][c] = vn;
+        if constexpr (P == 2) S[P - 1][rr][c] = vg;
+    }
+    __syncthreads();
+    const bool colok = (uint32_t)lane < tw;
+    const bool xw = warp < 4;
+    const uint32_t rbase = 8u * (uint32_t)(warp & 3) + 1;  // distances rbase .. rbase+7
+    int acc[8], acc2[8];          // carries of the carry-save sums (Blume-Capel: two chains)
+    uint32_t ones[8], ones2[8];   // sum bits
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc[d] = acc2[d] = 0, ones[d] = ones2[d] = 0;
+    long long zero = 0;           // distance 0 (Blume-Capel: non-zero sites)
+    for (uint32_t u = 0; u < kNearRows; u += 2) {
+        uint32_t a[2], an[2], ag[2], agn[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            a[h] = colok ? S[0][u + h][lane] : 0u;
+            an[h] = colok ? S[0][u + h][lane + 1] : 0u;
+            ag[h] = (P == 2 && colok) ? S[P - 1][u + h][lane] : 0u;
+            agn[h] = (P == 2 && colok) ? S[P - 1][u + h][lane + 1] : 0u;
+        }
+        if (MODEL == 1 && warp == 0) zero += __popc(a[0]) + __popc(a[1]);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const uint32_t r = rbase + d;
+            uint32_t b[2], bg[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (xw) {
+                    b[h] = r < 32 ? __funnelshift_r(a[h], an[h], r) : an[h];
+                    bg[h] = r < 32 ? __funnelshift_r(ag[h], agn[h], r) : agn[h];
+                } else {
+                    b[h] = colok ? S[0][u + h + r][lane] : 0u;
+                    bg[h] = (P == 2 && colok) ? S[P - 1][u + h + r][lane] : 0u;
+                }
+            }
+            if constexpr (MODEL == 0) {
+                const uint32_t x1 = a[0] ^ b[0], x2 = a[1] ^ b[1];
+                const uint32_t t = ones[d] ^ x1;
+                acc[d] += __popc((ones[d] & x1) | (t & x2));
+                ones[d] = t ^ x2;
+            } else {
+                // both = pairs of non-zero sites; neg = those of opposite sign
+                const uint32_t b1 = a[0] & b[0], b2 = a[1] & b[1];
+                const uint32_t n1 = b1 & (ag[0] ^ bg[0]), n2 = b2 & (ag[1] ^ bg[1]);
+                const uint32_t t = ones[d] ^ b1;
+                acc[d] += __popc((ones[d] & b1) | (t & b2));
+                ones[d] = t ^ b2;
+                const uint32_t t2 = ones2[d] ^ n1;
+                acc2[d] += __popc((ones2[d] & n1) | (t2 & n2));
+                ones2[d] = t2 ^ n2;
+            }
+        }
+    }
+    long long* out = xw ? cx : cy;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        long long v = MODEL == 0 ? 2ll * acc[d] + __popc(ones[d])  // unequal pairs
+                                 : (2ll * acc[d] + __popc(ones[d])) - 2 * (2ll * acc2[d] + __popc(ones2[d]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0 && rbase + d <= rmax) {
+            const long long pairs = (long long)kNearRows * 32 * tw;
+            const long long c = MODEL == 0 ? pairs - 2 * v : v;
+            atomicAdd(reinterpret_cast<unsigned long long*>(out + rbase + d), (unsigned long long)c);
+        }
+    }
+    if (warp == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) zero += __shfl_xor_sync(kFull, zero, o);
+        if (lane == 0) {
+            const long long c0 = MODEL == 0 ? (long long)kNearRows * 32 * tw : zero;
+            atomicAdd(reinterpret_cast<unsigned long long*>(cx), (unsigned long long)c0);
+            atomicAdd(reinterpret_cast<unsigned long long*>(cy), (unsigned long long)c0);
+        }
+    }
+}
+
 // Window sizes instantiated; the launcher picks the one that wastes the
 // fewest distance slots.
 constexpr int kNQ[] = {4, 8, 11, 13, 16};
@@ -408,6 +516,12 @@ cudaError_t launch_correlation(int model, const void* spins, uint32_t L, uint32_
     cudaError_t e = cudaMemsetAsync(cx, 0, (rmax + 1) * sizeof(long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cy, 0, (rmax + 1) * sizeof(long long), st);
     if (e != cudaSuccess) return e;
+    if (rmax <= kNear) {
+        const dim3 grid((L / 32 + 31) / 32, L / kNearRows);
+        if (model == 0) k_corr_near<0><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy);
+        else k_corr_near<1><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy);
+        return cudaGetLastError();
+    }
     return model == 0 ? launch_xy<0>(spins, L, rmax, cx, cy, st) : launch_xy<1>(spins, L, rmax, cx, cy, st);
 }
 
