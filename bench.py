@@ -57,6 +57,10 @@ WORKLOADS = {
     "ising-lut": dict(model=0, L=1 << 17, T=TC, Delta=0.0, seed=7, rmax=1024, rng=1,
                       name="ising-2d L=131072 T=Tc seed=7, the paper's lookup-table random bits: K sweeps, E/M every "
                            "sweep, C(r<=1024) x/y at sweeps 2^k"),
+    "ising-protocol": dict(model=0, L=1 << 17, T=TC, Delta=0.0, seed=7, rmax=32, protocol=16,
+                           name="ising-2d L=131072 T=Tc seed=7: K sweeps, E/M every sweep, C(r) by the section 3.3 "
+                                "protocol (all sites r<=32, one source per 16x16 square beyond, r_c(t), log-spaced r) "
+                                "at t=floor(2^(x/8)+0.5)"),
     "bc": dict(model=1, L=1 << 16, T=1.398, Delta=1.0, seed=99, rmax=512,
                name="blume-capel L=65536 Delta=1 T=1.398 seed=99: K sweeps, E/M/Q every sweep, C(r<=512) at sweeps 2^k"),
 }
@@ -172,15 +176,27 @@ def powers_of_two_upto(k: int):
     return out
 
 
-def run_job(lat, K: int, rmax: int, stream, with_corr: bool = True):
-    """K sweeps with per-sweep E/M and C(r) after sweeps 2^k; returns timing pieces.
+def run_job(lat, K: int, wl, stream, with_corr: bool = True):
+    """K sweeps with per-sweep E/M and C(r) at the workload's measurement times.
 
-    Returns (sweep_ms_total, n_sweep_launches, total_draws, n_corr, obs_count).
-    CUDA events bracket every lat_sweep call on the lattice's stream, so the
-    sweep-kernel time is measured on the stream the kernels run on."""
+    Measurement times are the sweeps 2^k (C(r <= rmax) from every site), or,
+    for the protocol workload, t = floor(2^(x/8) + 0.5) with the section 3.3
+    protocol.  Returns (sweep_ms_total, n_sweep_launches, total_draws,
+    n_corr_points, obs_count, corr_rows, corr_seconds, n_corr_launches).  CUDA events bracket
+    every lat_sweep call on the lattice's stream, so the sweep-kernel time is
+    measured on the stream the kernels run on."""
+    import numpy as np
     import torch
-    meas = powers_of_two_upto(K) if with_corr else set()
-    done, sweep_ms, draws, ncorr, nobs = 0, 0.0, 0, 0, 0
+
+    from paper_2502_18624_gb300 import binding as b
+    R = wl.get("protocol", 0)
+    if not with_corr:
+        meas = set()
+    elif R:
+        meas = set(int(t) for t in b.lat_protocol_times(K))
+    else:
+        meas = powers_of_two_upto(K)
+    done, sweep_ms, draws, nlaunch_corr, nobs, rows, corr_s, npts = 0, 0.0, 0, 0, 0, 0, 0.0, 0
     while done < K:
         nxt = min([m for m in meas if m > done], default=K)
         n = min(nxt, K) - done
@@ -194,9 +210,20 @@ def run_job(lat, K: int, rmax: int, stream, with_corr: bool = True):
         nobs += len(obs)
         done += n
         if done in meas:
-            lat.correlation(rmax)
-            ncorr += 1
-    return sweep_ms, 2 * K, draws, ncorr, nobs
+            t0 = time.perf_counter()
+            if R:
+                out = lat.correlation_protocol(done, R)
+                nds = int(np.sum(out["r"] > 2 * R))
+                rows += len(out["r"])
+                # near kernel, source-column copy, x and y launches per 2048 distances
+                nlaunch_corr += 1 + (1 if R >= 16 and nds else 0) + 2 * ((nds + 2047) // 2048)
+            else:
+                lat.correlation(wl["rmax"])
+                rows += wl["rmax"] + 1
+                nlaunch_corr += 1 if wl["rmax"] <= 32 else 2
+            corr_s += time.perf_counter() - t0
+            npts += 1
+    return sweep_ms, 2 * K, draws, npts, nobs, rows, corr_s, nlaunch_corr
 
 
 def native(args, wl):
@@ -226,7 +253,7 @@ def native(args, wl):
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     t_start.record(stream)
-    sweep_ms, nlaunch, draws, ncorr, _ = run_job(lat, K, wl["rmax"], stream)
+    sweep_ms, nlaunch, draws, ncorr, _, _, corr_s, corr_launches = run_job(lat, K, wl, stream)
     t_end.record(stream)
     torch.cuda.synchronize(device)
     clocks = sampler.stop()
@@ -255,7 +282,8 @@ def native(args, wl):
     if os.path.exists(prof) and not args.L:
         try:
             with open(prof) as f:
-                tr = json.load(f).get(args.workload, {})
+                # the protocol workload runs the same sweep launches as ising-tc
+                tr = json.load(f).get({"ising-protocol": "ising-tc"}.get(args.workload, args.workload), {})
             if tr.get("kernel_rev") == kernel_rev():
                 traffic = tr.get("bytes_per_launch")
         except Exception:
@@ -269,6 +297,7 @@ def native(args, wl):
                 "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "
                              "achieved counts 40 IMAD-ops per needed Philox block",
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
+    wl = dict(wl, corr_launches=corr_launches, corr_share=corr_s / max_secs)
     return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist,
                   batched)
 
@@ -337,13 +366,13 @@ def end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash):
     barrier(dist, device)
     t0 = time.perf_counter()
     b.lat_set_state(lat.handle, host_np)
-    _, _, _, ncorr_e2e, nobs = run_job(lat, K, wl["rmax"], stream)
+    _, _, _, _, nobs, corr_rows, _, _ = run_job(lat, K, wl, stream)
     b.lat_get_state(lat.handle, nbytes, host_np)
     torch.cuda.synchronize(device)
     e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
     assert lat.hash() == final_hash, "end-to-end run diverged from the device-resident run"
     lat.close()
-    d2h = nbytes + nobs * 40 + ncorr_e2e * 2 * (wl["rmax"] + 1) * 8
+    d2h = nbytes + nobs * 40 + corr_rows * (2 * 8 + (4 + 8 if wl.get("protocol") else 0))
     L2 = float(wl["L"]) ** 2
     return {"value": whole_job(L2 * K, world, e2e_secs), "unit": UNIT,
             "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
@@ -356,10 +385,12 @@ def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, rooflin
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl["name"].replace("K sweeps", "%d sweeps" % K), "L": wl["L"], "T": wl["T"],
                        "Delta": wl["Delta"], "seed": wl["seed"], "rmax": wl["rmax"], "sweeps": K,
-                       "correlation_points": ncorr, "parallelism": "replicas" if world > 1 else "single",
+                       "correlation_points": ncorr, "correlation_share_of_time": wl.get("corr_share"),
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (packed lattice %d MiB vs 126 MiB L2), no flush" %
                              (L2 / 8 / (1 << 20) * (1 if wl["model"] == 0 else 2))},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": nlaunch + 2 * ncorr, "clocks": clocks}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": nlaunch + wl.get("corr_launches", 2 * ncorr),
+            "clocks": clocks}
     if batched is not None:
         line["batched"] = batched
     if rank == 0:

@@ -319,8 +319,65 @@ constexpr uint32_t kNear = 32;
 constexpr uint32_t kNearRows = 64;
 constexpr uint32_t kNearStride = 33;  // 32 strip words + the next word
 
+// One warp's share of the near kernel: distances RB .. RB+7 (compile-time)
+// along x (X) or y, over all staged rows; m masks the lanes beyond the strip.
+template <int MODEL, bool X, int RB>
+__device__ __forceinline__ void near_rows(const uint32_t (*Sn)[kNearStride], const uint32_t (*Sg)[kNearStride],
+                                          int lane, uint32_t m, long long* v)
+{
+    int acc[8], acc2[8];          // carries of the carry-save sums (Blume-Capel: two chains)
+    uint32_t ones[8], ones2[8];   // sum bits
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc[d] = acc2[d] = 0, ones[d] = ones2[d] = 0;
+#pragma unroll(MODEL == 0 ? 2 : 1)
+    for (uint32_t u = 0; u < kNearRows; u += 2) {
+        uint32_t a[2], an[2], ag[2], agn[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            a[h] = Sn[u + h][lane];
+            if (X) an[h] = Sn[u + h][lane + 1];
+            if (MODEL == 1) {
+                ag[h] = Sg[u + h][lane];
+                if (X) agn[h] = Sg[u + h][lane + 1];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int r = RB + d;
+            uint32_t b[2], bg[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (X) {
+                    b[h] = r < 32 ? __funnelshift_r(a[h], an[h], r) : an[h];
+                    if (MODEL == 1) bg[h] = r < 32 ? __funnelshift_r(ag[h], agn[h], r) : agn[h];
+                } else {
+                    b[h] = Sn[u + h + r][lane];
+                    if (MODEL == 1) bg[h] = Sg[u + h + r][lane];
+                }
+            }
+            if constexpr (MODEL == 0) {
+                const uint32_t x1 = (a[0] ^ b[0]) & m, x2 = (a[1] ^ b[1]) & m;
+                acc[d] += __popc((ones[d] & x1) | ((ones[d] ^ x1) & x2));
+                ones[d] = ones[d] ^ x1 ^ x2;
+            } else {
+                // pairs of non-zero sites, and those of opposite sign
+                const uint32_t b1 = a[0] & b[0] & m, b2 = a[1] & b[1] & m;
+                const uint32_t n1 = b1 & (ag[0] ^ bg[0]), n2 = b2 & (ag[1] ^ bg[1]);
+                acc[d] += __popc((ones[d] & b1) | ((ones[d] ^ b1) & b2));
+                ones[d] = ones[d] ^ b1 ^ b2;
+                acc2[d] += __popc((ones2[d] & n1) | ((ones2[d] ^ n1) & n2));
+                ones2[d] = ones2[d] ^ n1 ^ n2;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+        v[d] = MODEL == 0 ? 2ll * acc[d] + __popc(ones[d])  // unequal pairs
+                          : (2ll * acc[d] + __popc(ones[d])) - 2 * (2ll * acc2[d] + __popc(ones2[d]));
+}
+
 template <int MODEL>
-__global__ void __launch_bounds__(256) k_corr_near(const void* spins, uint32_t L, uint32_t rmax, long long* cx,
+__global__ void __launch_bounds__(256, MODEL == 0 ? 6 : 4) k_corr_near(const void* spins, uint32_t L, uint32_t rmax, long long* cx,
                                                    long long* cy)
 {
     constexpr int P = Planes<MODEL>::n;
@@ -331,6 +388,8 @@ __global__ void __launch_bounds__(256) k_corr_near(const void* spins, uint32_t L
     const uint32_t j0 = blockIdx.x * 32;
     const uint32_t tw = min(32u, W32 - j0);
     const uint32_t y0 = blockIdx.y * kNearRows;
+    // column words j0 .. j0+tw of rows y0 .. y0+NR-1 (word j0+tw is the one
+    // right of the strip, periodic); zero beyond
     for (uint32_t t = threadIdx.x; t < NR * kNearStride; t += blockDim.x) {
         const uint32_t rr = t / kNearStride, c = t % kNearStride;
         const uint64_t y = ((uint64_t)y0 + rr) % L;
@@ -340,74 +399,43 @@ __global__ void __launch_bounds__(256) k_corr_near(const void* spins, uint32_t L
         if constexpr (P == 2) S[P - 1][rr][c] = vg;
     }
     __syncthreads();
-    const bool colok = (uint32_t)lane < tw;
-    const bool xw = warp < 4;
-    const uint32_t rbase = 8u * (uint32_t)(warp & 3) + 1;  // distances rbase .. rbase+7
-    int acc[8], acc2[8];          // carries of the carry-save sums (Blume-Capel: two chains)
-    uint32_t ones[8], ones2[8];   // sum bits
-#pragma unroll
-    for (int d = 0; d < 8; ++d) acc[d] = acc2[d] = 0, ones[d] = ones2[d] = 0;
-    long long zero = 0;           // distance 0 (Blume-Capel: non-zero sites)
-    for (uint32_t u = 0; u < kNearRows; u += 2) {
-        uint32_t a[2], an[2], ag[2], agn[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            a[h] = colok ? S[0][u + h][lane] : 0u;
-            an[h] = colok ? S[0][u + h][lane + 1] : 0u;
-            ag[h] = (P == 2 && colok) ? S[P - 1][u + h][lane] : 0u;
-            agn[h] = (P == 2 && colok) ? S[P - 1][u + h][lane + 1] : 0u;
-        }
-        if (MODEL == 1 && warp == 0) zero += __popc(a[0]) + __popc(a[1]);
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const uint32_t r = rbase + d;
-            uint32_t b[2], bg[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (xw) {
-                    b[h] = r < 32 ? __funnelshift_r(a[h], an[h], r) : an[h];
-                    bg[h] = r < 32 ? __funnelshift_r(ag[h], agn[h], r) : agn[h];
-                } else {
-                    b[h] = colok ? S[0][u + h + r][lane] : 0u;
-                    bg[h] = (P == 2 && colok) ? S[P - 1][u + h + r][lane] : 0u;
-                }
-            }
-            if constexpr (MODEL == 0) {
-                const uint32_t x1 = a[0] ^ b[0], x2 = a[1] ^ b[1];
-                const uint32_t t = ones[d] ^ x1;
-                acc[d] += __popc((ones[d] & x1) | (t & x2));
-                ones[d] = t ^ x2;
-            } else {
-                // both = pairs of non-zero sites; neg = those of opposite sign
-                const uint32_t b1 = a[0] & b[0], b2 = a[1] & b[1];
-                const uint32_t n1 = b1 & (ag[0] ^ bg[0]), n2 = b2 & (ag[1] ^ bg[1]);
-                const uint32_t t = ones[d] ^ b1;
-                acc[d] += __popc((ones[d] & b1) | (t & b2));
-                ones[d] = t ^ b2;
-                const uint32_t t2 = ones2[d] ^ n1;
-                acc2[d] += __popc((ones2[d] & n1) | (t2 & n2));
-                ones2[d] = t2 ^ n2;
-            }
-        }
+    const uint32_t m = (uint32_t)lane < tw ? ~0u : 0u;
+    const uint32_t (*Sn)[kNearStride] = S[0];
+    const uint32_t (*Sg)[kNearStride] = S[P - 1];
+    long long v[8];
+    switch (warp) {
+        case 0: near_rows<MODEL, true, 1>(Sn, Sg, lane, m, v); break;
+        case 1: near_rows<MODEL, true, 9>(Sn, Sg, lane, m, v); break;
+        case 2: near_rows<MODEL, true, 17>(Sn, Sg, lane, m, v); break;
+        case 3: near_rows<MODEL, true, 25>(Sn, Sg, lane, m, v); break;
+        case 4: near_rows<MODEL, false, 1>(Sn, Sg, lane, m, v); break;
+        case 5: near_rows<MODEL, false, 9>(Sn, Sg, lane, m, v); break;
+        case 6: near_rows<MODEL, false, 17>(Sn, Sg, lane, m, v); break;
+        default: near_rows<MODEL, false, 25>(Sn, Sg, lane, m, v); break;
     }
+    const bool xw = warp < 4;
+    const uint32_t rbase = 8u * (uint32_t)(warp & 3) + 1;
     long long* out = xw ? cx : cy;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-        long long v = MODEL == 0 ? 2ll * acc[d] + __popc(ones[d])  // unequal pairs
-                                 : (2ll * acc[d] + __popc(ones[d])) - 2 * (2ll * acc2[d] + __popc(ones2[d]));
+        long long t = v[d];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
         if (lane == 0 && rbase + d <= rmax) {
             const long long pairs = (long long)kNearRows * 32 * tw;
-            const long long c = MODEL == 0 ? pairs - 2 * v : v;
+            const long long c = MODEL == 0 ? pairs - 2 * t : t;
             atomicAdd(reinterpret_cast<unsigned long long*>(out + rbase + d), (unsigned long long)c);
         }
     }
+    // distance 0: every site (Ising) or every non-zero site (Blume-Capel)
     if (warp == 0) {
+        long long z = 0;
+        if (MODEL == 1)
+            for (uint32_t u = 0; u < kNearRows; ++u) z += __popc(Sn[u][lane] & m);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) zero += __shfl_xor_sync(kFull, zero, o);
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(kFull, z, o);
         if (lane == 0) {
-            const long long c0 = MODEL == 0 ? (long long)kNearRows * 32 * tw : zero;
+            const long long c0 = MODEL == 0 ? (long long)kNearRows * 32 * tw : z;
             atomicAdd(reinterpret_cast<unsigned long long*>(cx), (unsigned long long)c0);
             atomicAdd(reinterpret_cast<unsigned long long*>(cy), (unsigned long long)c0);
         }
