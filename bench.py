@@ -53,7 +53,8 @@ WORKLOADS = {
     "ising-0.9tc": dict(model=0, L=1 << 17, T=0.9 * TC, Delta=0.0, seed=7, rmax=1024,
                         name="ising-2d L=131072 T=0.9Tc seed=7: K sweeps, E/M every sweep, C(r<=1024) at sweeps 2^k"),
     "ising-capacity": dict(model=0, L=1 << 19, T=TC, Delta=0.0, seed=7, rmax=1024,
-                           name="ising-2d L=524288 (2^38 spins, 32 GiB) T=Tc seed=7: K sweeps, E/M every sweep"),
+                           name="ising-2d L=524288 (2^38 spins, 32 GiB) T=Tc seed=7: K sweeps, E/M every sweep, "
+                                "C(r<=1024) x/y at sweeps 2^k"),
     "ising-lut": dict(model=0, L=1 << 17, T=TC, Delta=0.0, seed=7, rmax=1024, rng=1,
                       name="ising-2d L=131072 T=Tc seed=7, the paper's lookup-table random bits: K sweeps, E/M every "
                            "sweep, C(r<=1024) x/y at sweeps 2^k"),
