@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
 {
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
-    __shared__ unsigned long long s_thr[72];
+    __shared__ unsigned long long s_thr[kBcTable];
     __shared__ uint32_t s_lut[16];
     const unsigned long long total = ctl->total;
     const uint32_t K = ctl->nphases;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
             if (*(volatile unsigned int*)&ctl->error) stop = 1;
             s_stop = stop;
         }
-        if (d.model == 1) bc_table72(d.bc_thr, s_thr);
+        if (d.model == 1) bc_table128(d.bc_thr, s_thr);
         else if (d.rng == LAT_RNG_TABLE_MODE && threadIdx.x < 16) s_lut[threadIdx.x] = d.lut[threadIdx.x];
         __syncthreads();
         if (s_stop) break;

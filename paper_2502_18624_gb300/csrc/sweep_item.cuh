@@ -313,30 +313,42 @@ __device__ __forceinline__ void add4(U a, U b, U c, U d, U& b0, U& b1, U& b2)
 }
 
 // A Blume-Capel spin's 2-bit code is n | g << 1 (n: s != 0, g: s = -1):
-// 0 for s = 0, 1 for s = +1, 3 for s = -1 (2 never occurs).  The kernels
-// index their acceptance table by (code, proposal bit b, h + 4):
-// entry (code*2 + b)*9 + h+4, 72 entries with code 2 unused; see
-// bc_table72.  kBcNext gives the code of the proposed value, the b-th of the
-// two other values in ascending order, at index code*2 + b (2 bits each):
-// s=0 -> {-1, +1}, s=+1 -> {-1, 0}, s=-1 -> {0, +1}.
+// 0 for s = 0, 1 for s = +1, 3 for s = -1 (2 never occurs).  kBcNext gives
+// the code of the proposed value, the b-th of the two other values in
+// ascending order, at index code*2 + b (2 bits each): s=0 -> {-1, +1},
+// s=+1 -> {-1, 0}, s=-1 -> {0, +1}.
 constexpr uint32_t kBcNext = (3u << 0) | (1u << 2) | (3u << 4) | (0u << 6) | (0u << 8) | (0u << 10) |
                              (0u << 12) | (1u << 14);
 
-// Expand the 54-entry table (index ((s+1)*2 + b)*9 + h+4) to the 72-entry
-// code-indexed one, in shared memory.
-__device__ __forceinline__ void bc_table72(const unsigned long long* thr54, unsigned long long* s_thr)
-{
-    for (int i = threadIdx.x; i < 72; i += blockDim.x) {
-        const int code = i / 18, b = (i / 9) % 2, h = i % 9;
-        const int s = code == 0 ? 0 : (code == 1 ? 1 : -1);
-        s_thr[i] = code == 2 ? 0ull : thr54[((s + 1) * 2 + b) * 9 + h];
-    }
-}
-
 // Value of a 2-bit spin code: 0, +1 or -1.
-__device__ __forceinline__ int bc_value(uint32_t code)
+__host__ __device__ __forceinline__ int bc_value(uint32_t code)
 {
     return (int)(code & 1u) * (1 - (int)(code & 2u));
+}
+
+// The kernels' Blume-Capel table, 128 entries indexed by
+//   code | (h+4) << 2 | b << 6
+// (spin code, neighbour sum h = -4..4 as h+4 in 4 bits, proposal bit b).
+// Entry bits 0..32: the acceptance bound of the 54-entry table (2^32 =
+// always); bits 40..41: code of the proposed value; bits 48..55 and 56..63:
+// s'*h and s*h as signed bytes (the site's share of the bond sum B if the
+// move is accepted or rejected).  Unused indices (code 2, h+4 > 8) hold 0.
+constexpr int kBcTable = 128;
+
+__device__ __forceinline__ void bc_table128(const unsigned long long* thr54, unsigned long long* t)
+{
+    for (int i = threadIdx.x; i < kBcTable; i += blockDim.x) {
+        const uint32_t code = i & 3u, h4 = (i >> 2) & 15u, b = (uint32_t)i >> 6;
+        unsigned long long e = 0;
+        if (code != 2u && h4 <= 8u) {
+            const int sv = bc_value(code), h = (int)h4 - 4;
+            const uint32_t next = (kBcNext >> (2u * (code * 2u + b))) & 3u;
+            e = thr54[((sv + 1) * 2 + (int)b) * 9 + (int)h4] | ((unsigned long long)next << 40) |
+                ((unsigned long long)(uint8_t)(int8_t)(bc_value(next) * h) << 48) |
+                ((unsigned long long)(uint8_t)(int8_t)(sv * h) << 56);
+        }
+        t[i] = e;
+    }
 }
 
 struct BcPhase {
@@ -348,15 +360,18 @@ struct BcPhase {
 // Blume-Capel decision (Eq. (2)): every active site draws; the low bit of
 // word 1 picks the proposal among the two other values, and the move is
 // accepted iff the table entry for (s, proposal, h) is 2^32 or word 0 is
-// below it.  s_thr is the 72-entry code-indexed table (bc_table72) in shared
-// memory; the update is branch-free.
+// below it.  The update is branch-free.
 //
 // Every plane is first shifted right by the row's colour parity, so the 32
-// active sites sit at the even bit positions, and each 32-bit half is handled
-// in turn.  The fused bond sum (colour 1) adds s' * h per active site, h the
-// final neighbour sum (its four neighbours are colour 0 and already final).
+// active sites sit at the even bit positions.  A site's table index is
+// built once per item, bit-sliced for all 64 positions: h + 4 = 2 P + Z,
+// with P (Z) the number of +1 (zero) neighbours, so h+4 needs no
+// subtraction.  Two planes share one word (one at the even, one at the odd
+// positions), so three shifts give a site's code and h+4.  The fused bond
+// sum (colour 1) adds s' * h per active site, h the final neighbour sum (its
+// four neighbours are colour 0 and already final).
 template <bool OBS, bool CG>
-__device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const unsigned long long* s_thr,
+__device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const unsigned long long* s_tab,
                                         uint64_t item, int lane, PhaseAcc& acc)
 {
     const uint32_t y = (uint32_t)(item / a.W);
@@ -376,53 +391,53 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
     if (lane == 31 || j + 1 == a.W) right = ld<CG>(row + (j + 1 == a.W ? 0 : j + 1));
 
     const uint32_t p = (y + a.colour) & 1u;
-    // Planes in the shifted frame (active sites at even positions).  The
-    // neighbour sum of a site is h = P - N: P (N) counts its +1 (-1)
-    // neighbours, kept as three bit-sliced 64-bit words each.
-    const uint64_t Cn = c.x >> p, Cg = c.y >> p;
-    uint64_t P0, P1, P2, N0, N1, N2;
+    // Planes in the shifted frame (active sites at even positions).
+    uint64_t wcode, wh01, wh23;  // code; h+4 bits 0,1; h+4 bits 2,3 (even/odd positions)
     {
         const uint64_t nn_ = vn.x >> p, ng_ = vn.y >> p, sn_ = vs.x >> p, sg_ = vs.y >> p;
         const uint64_t wn_ = ((c.x << 1) | (left.x >> 63)) >> p, wg_ = ((c.y << 1) | (left.y >> 63)) >> p;
         const uint64_t en_ = ((c.x >> 1) | (right.x << 63)) >> p, eg_ = ((c.y >> 1) | (right.y << 63)) >> p;
+        uint64_t P0, P1, P2, Z0, Z1, Z2;
         add4<uint64_t>(nn_ & ~ng_, sn_ & ~sg_, wn_ & ~wg_, en_ & ~eg_, P0, P1, P2);
-        add4<uint64_t>(nn_ & ng_, sn_ & sg_, wn_ & wg_, en_ & eg_, N0, N1, N2);
+        add4<uint64_t>(~nn_, ~sn_, ~wn_, ~en_, Z0, Z1, Z2);
+        // h+4 = Z + 2P, bit-sliced (at most 8: no carry out of bit 3)
+        const uint64_t s1 = Z1 ^ P0, c1 = Z1 & P0;
+        const uint64_t s2 = Z2 ^ P1 ^ c1, c2 = (Z2 & P1) | (Z2 & c1) | (P1 & c1);
+        const uint64_t s3 = P2 ^ c2;
+        constexpr uint64_t E = kEvenBits;
+        wcode = ((c.x >> p) & E) | (((c.y >> p) & E) << 1);
+        wh01 = (Z0 & E) | ((s1 & E) << 1);
+        wh23 = (s2 & E) | ((s3 & E) << 1);
     }
 
     const uint64_t base = (uint64_t)y * a.L + (uint64_t)j * 64u;
     const uint32_t site0 = (uint32_t)base + p;  // site of shifted position 0
     const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
-    uint64_t acc_m = 0, acc_n = 0, acc_g = 0;  // accepted sites, their new n and g bits (shifted frame)
-    int bsum = 0;                              // sum over active sites of s' * h (fused bond sum)
+    uint64_t acc_m = 0, acc_c = 0;  // accepted sites (even positions); their new codes (2 bits each)
+    int bsum = 0;                   // sum over active sites of s' * h (fused bond sum)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int hs = 32 * half;
-        const uint32_t cn = (uint32_t)(Cn >> hs), cg = (uint32_t)(Cg >> hs);
-        const uint32_t p0 = (uint32_t)(P0 >> hs), p1 = (uint32_t)(P1 >> hs), p2 = (uint32_t)(P2 >> hs);
-        const uint32_t q0 = (uint32_t)(N0 >> hs), q1 = (uint32_t)(N1 >> hs), q2 = (uint32_t)(N2 >> hs);
-        uint32_t am = 0, an = 0, ag = 0;
+        const uint32_t x0 = (uint32_t)(wcode >> hs), x1 = (uint32_t)(wh01 >> hs), x2 = (uint32_t)(wh23 >> hs);
+        uint32_t am = 0, ac = 0;
 #pragma unroll 2
         for (int k = 0; k < 16; ++k) {
             const uint32_t b = 2u * k;
-            const uint32_t code = ((cn >> b) & 1u) | (((cg >> b) & 1u) << 1);
-            const uint32_t P = ((p0 >> b) & 1u) | (((p1 >> b) & 1u) << 1) | (((p2 >> b) & 1u) << 2);
-            const uint32_t N = ((q0 >> b) & 1u) | (((q1 >> b) & 1u) << 1) | (((q2 >> b) & 1u) << 2);
             const uint2 r = philox_site_w01(site0 + (uint32_t)hs + b, pc, rk);
-            const uint32_t mv = code * 2u + (r.y & 1u);
-            const bool accept = (unsigned long long)r.x < s_thr[mv * 9u + 4u + P - N];
-            const uint32_t next = (kBcNext >> (2u * mv)) & 3u;
-            const uint32_t bit = accept ? (1u << b) : 0u;
-            am |= bit;
-            an |= (next & 1u) ? bit : 0u;
-            ag |= (next & 2u) ? bit : 0u;
-            if constexpr (OBS) bsum += bc_value(accept ? next : code) * ((int)P - (int)N);
+            const uint32_t idx = ((x0 >> b) & 3u) | (((x1 >> b) & 3u) << 2) | (((x2 >> b) & 3u) << 4) |
+                                 ((r.y & 1u) << 6);
+            const unsigned long long e = s_tab[idx];
+            const uint32_t accept = ((uint32_t)(e >> 32) & 1u) | (r.x < (uint32_t)e ? 1u : 0u);
+            am |= accept << b;
+            ac |= (accept ? (uint32_t)(e >> 40) & 3u : 0u) << b;
+            if constexpr (OBS) bsum += accept ? (int)(int8_t)(e >> 48) : (int)(int8_t)(e >> 56);
         }
         acc_m |= (uint64_t)am << hs;
-        acc_n |= (uint64_t)an << hs;
-        acc_g |= (uint64_t)ag << hs;
+        acc_c |= (uint64_t)ac << hs;
     }
+    constexpr uint64_t E = kEvenBits;
     const uint64_t m = acc_m << p;
-    const uint64_t nn = (c.x & ~m) | (acc_n << p), gg = (c.y & ~m) | (acc_g << p);
+    const uint64_t nn = (c.x & ~m) | ((acc_c & E) << p), gg = (c.y & ~m) | (((acc_c >> 1) & E) << p);
     row[j] = make_ulonglong2(nn, gg);
     acc.D += 32;
     if constexpr (OBS) {
