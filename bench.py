@@ -263,6 +263,8 @@ def native(args, wl):
     max_secs = reduce_max(dist, secs, device)
     L2 = float(wl["L"]) ** 2
     value = whole_job(L2 * K, world, max_secs)
+    counts = lat.spin_counts()  # consistency check: every site holds a spin, L^2 in total
+    assert counts[3] == 0 and int(counts[:3].sum()) == wl["L"] ** 2, "spin counts inconsistent: %s" % counts
     final_hash = lat.hash()
     lat.close()
 

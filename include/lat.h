@@ -218,6 +218,15 @@ int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr
 int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uint32_t* n_out, uint32_t* r_out,
                              int64_t* cx, int64_t* cy, uint64_t* nsrc);
 
+/* Spin counts, the consistency check the paper's runs perform (Table 3
+ * caption: the total number of spins stays unchanged): counts[0], [1], [2]
+ * = number of sites holding -1, 0, +1, and counts[3] = number of
+ * Blume-Capel 2-bit codes that are not a spin (g set without n; always 0 for
+ * Ising).  On a sound lattice counts[0] + counts[1] + counts[2] = L^2,
+ * counts[3] = 0, M = counts[2] - counts[0] and Q = counts[0] + counts[2].
+ * Synchronises. */
+int lat_spin_counts(lat_t* h, int64_t counts[4]);
+
 /* Schwinger-Dyson histogram of Eq. (3): hist[v+4] = number of sites with
  * s_x * h_x = v, v = -4..4, h_x the sum of the four neighbours.  Eq. (3)'s
  * right-hand side is L^-2 sum_v hist[v+4] exp(-2 J v / T).  hist is a host
@@ -251,7 +260,10 @@ size_t lat_state_bytes(const lat_params* p);
  * L rows of L/64 little-endian uint64 words, bit b of word j = site 64j+b,
  * set iff s = +1; Blume-Capel, L rows of L/64 word pairs (plane n: s != 0,
  * plane g: s = -1), pair j covering sites 64j..64j+63.  bytes must equal
- * lat_state_bytes.  Host memory may be pinned or pageable.  Synchronises. */
+ * lat_state_bytes.  Host memory may be pinned or pageable.  lat_set_state
+ * copies the words as they are (a Blume-Capel pair with g set and n clear
+ * is not a spin; lat_spin_counts reports how many there are).
+ * Synchronises. */
 int lat_get_state(lat_t* h, void* host, size_t bytes);
 int lat_set_state(lat_t* h, const void* host, size_t bytes);
 

@@ -76,6 +76,7 @@ def load(build_if_missing: bool = True):
         "lat_correlation_sampled": (i32, [P, u32, P, u32, P, P]),
         "lat_correlation_protocol": (i32, [P, u64, u32, u32, P, P, P, P, P]),
         "lat_sd_hist": (i32, [P, P]),
+        "lat_spin_counts": (i32, [P, P]),
         "lat_hash": (i32, [P, P]),
         "lat_get_spins": (i32, [P, P]),
         "lat_get_rows": (i32, [P, u32, u32, P]),
@@ -211,6 +212,13 @@ def lat_correlation_protocol(h, t: int, R: int = 16) -> dict:
     return {"r": r, "cx": cx, "cy": cy, "nsrc": ns}
 
 
+def lat_spin_counts(h) -> np.ndarray:
+    """Sites holding -1, 0, +1, and invalid Blume-Capel codes (int64[4])."""
+    out = np.zeros(4, dtype=np.int64)
+    _check(load().lat_spin_counts(h, _ptr(out)), "lat_spin_counts")
+    return out
+
+
 def lat_sd_hist(h) -> np.ndarray:
     out = np.zeros(9, dtype=np.int64)
     _check(load().lat_sd_hist(h, _ptr(out)), "lat_sd_hist")
@@ -307,6 +315,9 @@ class Lattice:
 
     def sd_hist(self):
         return lat_sd_hist(self.handle)
+
+    def spin_counts(self) -> np.ndarray:
+        return lat_spin_counts(self.handle)
 
     def hash(self) -> int:
         return lat_hash(self.handle)

@@ -92,6 +92,37 @@ __global__ void __launch_bounds__(kThreads) k_measure(const void* spins, uint32_
     }
 }
 
+// Number of sites holding each spin value (the consistency check of the
+// paper's runs: the counts of -1, 0 and +1 add up to L^2), and the number of
+// Blume-Capel words' 2-bit codes that are not a spin (g set without n).
+template <int MODEL>
+__global__ void __launch_bounds__(kThreads) k_spin_counts(const void* spins, uint32_t L, uint32_t W, long long* out)
+{
+    long long neg = 0, zero = 0, pos = 0, bad = 0;
+    const uint64_t nwords = (uint64_t)L * W;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if constexpr (MODEL == 0) {
+            const int up = __popcll(static_cast<const uint64_t*>(spins)[i]);
+            pos += up;
+            neg += 64 - up;
+        } else {
+            const ulonglong2 c = static_cast<const ulonglong2*>(spins)[i];
+            pos += __popcll(c.x & ~c.y);
+            neg += __popcll(c.x & c.y);
+            zero += __popcll(~c.x & ~c.y);
+            bad += __popcll(~c.x & c.y);
+        }
+    }
+    neg = warp_sum(neg); zero = warp_sum(zero); pos = warp_sum(pos); bad = warp_sum(bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 0), (unsigned long long)neg);
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 1), (unsigned long long)zero);
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 2), (unsigned long long)pos);
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 3), (unsigned long long)bad);
+    }
+}
+
 // Histogram of s_x * h_x (Eq. (3)), bins v = -4..4 at v + 4.
 template <int MODEL>
 __global__ void __launch_bounds__(kThreads) k_sd_hist(const void* spins, uint32_t L, uint32_t W, long long* hist)
@@ -252,6 +283,17 @@ cudaError_t launch_measure(int model, const void* spins, uint32_t L, uint32_t W,
     const int grid = grid_for((uint64_t)L * W, sms, 8);
     if (model == 0) k_measure<0><<<grid, kThreads, 0, st>>>(spins, L, W, out3);
     else k_measure<1><<<grid, kThreads, 0, st>>>(spins, L, W, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spin_counts(int model, const void* spins, uint32_t L, uint32_t W, long long* out4, int sms,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out4, 0, 4 * sizeof(long long), st);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((uint64_t)L * W, sms, 8);
+    if (model == 0) k_spin_counts<0><<<grid, kThreads, 0, st>>>(spins, L, W, out4);
+    else k_spin_counts<1><<<grid, kThreads, 0, st>>>(spins, L, W, out4);
     return cudaGetLastError();
 }
 

@@ -386,6 +386,15 @@ int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uin
     return lat_correlation_sampled(h, R, r_out + rfull + 1, nds, cx + rfull + 1, cy + rfull + 1);
 }
 
+int lat_spin_counts(lat_t* h, int64_t counts[4])
+{
+    if (!h || !counts) return LAT_EINVAL;
+    cudaError_t e = launch_spin_counts(h->p.model, h->spins(), h->p.L, h->W, h->misc() + 24, h->ls.sms, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, h->misc() + 24, 4 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_err(e);
+}
+
 int lat_sd_hist(lat_t* h, int64_t* hist)
 {
     if (!h || !hist) return LAT_EINVAL;

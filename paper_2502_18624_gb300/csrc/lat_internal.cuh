@@ -64,6 +64,8 @@ cudaError_t launch_init(int model, void* spins, uint32_t L, uint32_t W, const Ro
                         cudaStream_t st);
 cudaError_t launch_measure(int model, const void* spins, uint32_t L, uint32_t W, long long* out3, int sms,
                            cudaStream_t st);
+cudaError_t launch_spin_counts(int model, const void* spins, uint32_t L, uint32_t W, long long* out4, int sms,
+                               cudaStream_t st);
 cudaError_t launch_sd_hist(int model, const void* spins, uint32_t L, uint32_t W, long long* hist9, int sms,
                            cudaStream_t st);
 cudaError_t launch_hash(int model, const void* spins, uint32_t L, uint32_t W, unsigned long long* out, int sms,

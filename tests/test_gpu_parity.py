@@ -228,3 +228,39 @@ def test_capacity_point_L2p19(gpu, orc):
     M, B, Q, _ = lat.measure()
     assert (int(obs["M"][0]), int(obs["B"][0]), Q) == (M, B, L * L)
     lat.close()
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_spin_counts_and_invalid_codes(gpu, orc, model):
+    """The spin-count consistency check: per-value counts against the
+    oracle's lattice, their sum L^2, and (Blume-Capel) a 2-bit code that is
+    not a spin, planted in the raw state, is counted and nothing else moves."""
+    T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
+    L = 192
+    lat = b.Lattice(model, L, T, 21, Delta=Delta)
+    lat.sweep(7, record=False)
+    s = lat.spins()
+    counts = lat.spin_counts()
+    assert counts.tolist() == [int((s == -1).sum()), int((s == 0).sum()), int((s == 1).sum()), 0]
+    M, B, Q, _ = lat.measure()
+    assert counts[:3].sum() == L * L and M == counts[2] - counts[0] and Q == counts[0] + counts[2]
+    if model == 1:
+        st = lat.state().view(np.uint64).copy()
+        n0, g0 = int(st[0]), int(st[1])          # word pair (row 0, word 0): n plane, g plane
+        zero_bit = next(i for i in range(64) if not (n0 >> i) & 1)
+        st[1] = np.uint64(g0 | (1 << zero_bit))  # g without n at a zero site
+        lat.set_state(st.view(np.uint8))
+        bad = lat.spin_counts()
+        assert bad[3] == 1 and bad[1] == counts[1] - 1 and bad[0] == counts[0] and bad[2] == counts[2]
+    lat.close()
+
+
+@pytest.mark.parametrize("model,L", [(0, 1 << 17), (1, 1 << 16)])
+def test_spin_counts_full_size(gpu, model, L):
+    T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
+    lat = b.Lattice(model, L, T, 5, Delta=Delta)
+    obs = lat.sweep(2)
+    counts = lat.spin_counts()
+    assert counts[:3].sum() == L * L and counts[3] == 0
+    assert int(obs["M"][-1]) == counts[2] - counts[0] and int(obs["Q"][-1]) == counts[0] + counts[2]
+    lat.close()
