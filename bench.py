@@ -478,6 +478,7 @@ def served_bench(args):
     barrier(dist, device)
     res = srv.run(jobs)
     clocks = sampler.stop()
+    srv_launches = eng.launches
     eng.close()
     s_srv = serve.summarize(res, srv.wall)
     seq_eng = serve.GpuEngine(1, 1)
@@ -485,6 +486,7 @@ def served_bench(args):
     t0 = time.perf_counter()
     seq = serve.run_sequential(seq_eng, jobs)
     seq_wall = time.perf_counter() - t0
+    seq_launches = seq_eng.launches
     seq_eng.close()
     s_seq = serve.summarize(seq, seq_wall)
     exact = all(serve.same_results(a, b) for a, b in zip(res, seq))
@@ -501,8 +503,8 @@ def served_bench(args):
                            "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch,
                            "step_updates": args.step_updates, "parallelism": "replicas" if world > 1 else "single"},
                 "served": dict(s_srv, steps=srv.steps, peak_batch=srv.peak_batch, peak_mem=srv.peak_mem),
-                "sequential_plain": s_seq, "bit_exact": exact, "clocks": clocks,
-                "gpu_launches": None}
+                "sequential_plain": dict(s_seq, gpu_launches=seq_launches), "bit_exact": exact, "clocks": clocks,
+                "gpu_launches": srv_launches}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

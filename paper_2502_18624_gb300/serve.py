@@ -78,20 +78,31 @@ class GpuEngine:
             for (m, L), t in tiles.items():
                 self.runner.set_tile(m, L, t)
         self.rmax_cap = rmax_cap
+        self.launches = 0  # kernels launched: quench, runner runs, correlation, hash
 
     def footprint(self, job) -> int:
         return self.b.lat_footprint(self.b.make_params(job.model, job.L, job.T, job.seed, Delta=job.Delta))
 
     def create(self, job):
+        self.launches += 1
         return self.b.Lattice(job.model, job.L, job.T, job.seed, Delta=job.Delta, stream=self.runner.stream)
 
     def advance(self, handles, nsweeps):
+        self.launches += 1 if any(nsweeps) else 0
         return self.runner.run(handles, nsweeps)
 
     def measure(self, h):
-        return h.correlation(min(h.L // 2, self.rmax_cap))
+        rmax = min(h.L // 2, self.rmax_cap)
+        self.launches += 1 if rmax <= 32 else 2
+        return h.correlation(rmax)
+
+    def sweep(self, h, n: int):
+        """The one-lattice path (sequential baseline): two phase launches per sweep."""
+        self.launches += 2 * n
+        return h.sweep(n)
 
     def finish(self, h) -> int:
+        self.launches += 1
         v = h.hash()
         h.close()
         return v
@@ -184,7 +195,7 @@ def run_sequential(engine, jobs, clock=time.perf_counter, sleep=time.sleep):
         done = 0
         while done < j.sweeps:
             k = min(j.sweeps, next_measurement(done)) - done
-            r.obs.append(h.sweep(k))
+            r.obs.append(engine.sweep(h, k) if hasattr(engine, "sweep") else h.sweep(k))
             done += k
             if (done & (done - 1)) == 0:
                 r.corr[done] = engine.measure(h)
