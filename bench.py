@@ -415,7 +415,7 @@ def measured_hbm_gbs() -> float:
 def kernel_rev() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("k_sweep.cu", "sweep_item.cuh", "philox.cuh", "lat_internal.cuh"):
+    for name in ("k_sweep.cu", "sweep_item.cuh", "philox.cuh", "sweep_args.cuh"):
         with open(os.path.join(ROOT, "paper_2502_18624_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

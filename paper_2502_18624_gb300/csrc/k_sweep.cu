@@ -10,6 +10,7 @@
 // (L * W / CW, or L * W) is a multiple of 32.  The fused E/M/Q reduction
 // (colour-1 phase) and the draw count are reduced per warp and added with
 // one atomic per warp.
+#include "lat_internal.cuh"
 #include "sweep_item.cuh"
 
 namespace latk {

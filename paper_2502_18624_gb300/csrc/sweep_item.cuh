@@ -19,7 +19,7 @@
 // runs many phases in one launch, and a block may read a row it cached in
 // L1 during an earlier phase, so it bypasses L1.
 #pragma once
-#include "lat_internal.cuh"
+#include "sweep_args.cuh"
 
 namespace latk {
 
