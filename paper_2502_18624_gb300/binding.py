@@ -352,6 +352,7 @@ class Lattice:
         if getattr(self, "handle", None):
             lat_destroy(self.handle)
             self.handle = None
+        self.buffer = None  # the device buffer goes back to torch's allocator
 
     def __enter__(self):
         return self

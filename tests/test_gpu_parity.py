@@ -264,3 +264,45 @@ def test_spin_counts_full_size(gpu, model, L):
     assert counts[:3].sum() == L * L and counts[3] == 0
     assert int(obs["M"][-1]) == counts[2] - counts[0] and int(obs["Q"][-1]) == counts[0] + counts[2]
     lat.close()
+
+
+@pytest.mark.parametrize("model,L", [(0, 1 << 20), (1, 1 << 19)])
+def test_maximum_sizes(gpu, orc, model, L):
+    """The largest lattices the library accepts: Ising L = 2^20 (2^40 spins,
+    128 GiB packed) and Blume-Capel L = 2^19 (2^38 spins, 64 GiB).  Quench
+    rows at both ends, one-sweep transitions on windows at the top, the
+    periodic seam and the last rows (site indices near L^2), and whole-lattice
+    invariants."""
+    T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
+    seed = 13
+    lat = b.Lattice(model, L, T, seed, Delta=Delta)
+    thr = orc.thresholds(model, 1.0, T, Delta)
+    for y0 in (0, L - 2):
+        assert np.array_equal(lat.rows(y0, 2), orc.init_rows(model, L, seed, y0, 2))
+    obs = _transition_check(orc, lat, model, L, seed, thr, [0, L - 4, L // 3], H=4)
+    M, B, Q, _ = lat.measure()
+    assert (int(obs["M"][0]), int(obs["B"][0]), int(obs["Q"][0])) == (M, B, Q)
+    counts = lat.spin_counts()
+    assert counts[:3].sum() == L * L and counts[3] == 0 and M == counts[2] - counts[0]
+    cx, cy = lat.correlation(1)
+    assert cx[1] + cy[1] == B
+    lat.close()
+    import torch
+    torch.cuda.empty_cache()  # return the 64-128 GiB to the device for the tests that follow
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_empty_calls_change_nothing(gpu, model):
+    T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
+    lat = b.Lattice(model, 128, T, 3, Delta=Delta)
+    lat.sweep(3, record=False)
+    h0, t0 = lat.hash(), lat.sweep_index
+    assert lat.sweep(0).size == 0 and lat.sweep(0, record=False) is None
+    cx, cy = lat.correlation(0)
+    assert cx[0] == cy[0] == lat.spin_counts()[[0, 2]].sum()
+    assert lat.correlation_sampled(16, [])[0].size == 0
+    r = b.Runner(2, 4)
+    assert r.run([lat], [0]) is not None
+    r.close()
+    assert lat.hash() == h0 and lat.sweep_index == t0
+    lat.close()
