@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_c
 template <int CW, bool OBS>
 __global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
 {
-    __shared__ uint32_t s_lut[16];
-    if (threadIdx.x < 16) s_lut[threadIdx.x] = a.lut[threadIdx.x];
+    __shared__ uint32_t s_lut[kLutSlots];
+    if (threadIdx.x < kLutSlots) s_lut[threadIdx.x] = lut_slot(a.lut, threadIdx.x);
     __syncthreads();
     const IsingPhase ph{a.spins, a.L, a.W, a.sweep, a.colour, a.thr4, a.thr8, a.mode4, a.mode8};
     const uint64_t nitems = (uint64_t)a.L * (a.W / CW);

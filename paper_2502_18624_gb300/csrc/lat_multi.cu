@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
     __shared__ unsigned long long s_thr[kBcTable];
-    __shared__ uint32_t s_lut[16];
+    __shared__ uint32_t s_lut[kLutSlots];
     const unsigned long long total = ctl->total;
     const uint32_t K = ctl->nphases;
     for (;;) {
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
             s_stop = stop;
         }
         if (d.model == 1) bc_table128(d.bc_thr, s_thr);
-        else if (d.rng == LAT_RNG_TABLE_MODE && threadIdx.x < 16) s_lut[threadIdx.x] = d.lut[threadIdx.x];
+        else if (d.rng == LAT_RNG_TABLE_MODE && threadIdx.x < kLutSlots) s_lut[threadIdx.x] = lut_slot(d.lut, threadIdx.x);
         __syncthreads();
         if (s_stop) break;
 

@@ -240,36 +240,44 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
     ising_finish<CW, OBS>(it, acc);
 }
 
-// Index of the largest entry not above u in the sorted 16-entry table
-// (entry 0 is 0): a four-step binary search.
-__device__ __forceinline__ uint32_t lut_find(const uint32_t* t, uint32_t u)
+// The 16-entry table is searched in "spread" form: entry j sits at slot
+// spread4(j) (bit k of j moved to bit 2k) of an 86-slot shared array, so the
+// binary search yields the four random bits already at the even positions
+// of a byte, where the word's active sites take them (no later spreading).
+constexpr int kLutSlots = 86;  // spread4(15) + 1
+
+__host__ __device__ __forceinline__ constexpr uint32_t spread4(uint32_t j)
 {
-    uint32_t j = u >= t[8] ? 8u : 0u;
-    j += u >= t[j + 4] ? 4u : 0u;
-    j += u >= t[j + 2] ? 2u : 0u;
-    j += u >= t[j + 1] ? 1u : 0u;
-    return j;
+    return (j & 1u) | ((j & 2u) << 1) | ((j & 4u) << 2) | ((j & 8u) << 3);
 }
 
-// Bit k of x to bit 2k of the result.
-__device__ __forceinline__ uint64_t spread_even(uint32_t v)
+// Slot i of the spread table built from the 16 entries t16 (0 where i is
+// not spread4 of any index).
+__device__ __forceinline__ uint32_t lut_slot(const uint32_t* t16, uint32_t i)
 {
-    uint64_t x = v;
-    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
-    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
-    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
-    x = (x | (x << 2)) & 0x3333333333333333ull;
-    x = (x | (x << 1)) & 0x5555555555555555ull;
-    return x;
+    if (i & 0xAAu) return 0u;
+    return t16[(i & 1u) | ((i >> 1) & 2u) | ((i >> 2) & 4u) | ((i >> 3) & 8u)];
+}
+
+// spread4 of the largest index j with t[j] <= u (t[0] = 0): a four-step
+// binary search over the spread table.
+__device__ __forceinline__ uint32_t lut_find_spread(const uint32_t* ts, uint32_t u)
+{
+    uint32_t js = u >= ts[spread4(8)] ? spread4(8) : 0u;
+    js += u >= ts[js + spread4(4)] ? spread4(4) : 0u;
+    js += u >= ts[js + spread4(2)] ? spread4(2) : 0u;
+    js += u >= ts[js + spread4(1)] ? spread4(1) : 0u;
+    return js;
 }
 
 // The paper's lookup-table random bits (section 3.2, LAT_RNG_TABLE): per
 // 64-bit word, four Philox blocks (counters 4w+q, sweep, colour+2) give 16
-// uniforms; each is located in the table s_lut, and the index is four
-// random bits.  Uniforms 0..7 build word e0, 8..15 word e1 (bits 4i..4i+3
-// from uniform i), whose bit k belongs to the word's k-th active site.  A
-// 3-agree site flips iff its e0 bit is set, a 4-agree site iff its e0 and
-// e1 bits are.
+// uniforms; each is located in the table s_lut (spread form, kLutSlots
+// slots), and the index is four random bits.  Uniforms 0..7 build word e0,
+// 8..15 word e1: uniform i gives the bits of the word's active sites 4i ..
+// 4i+3, which sit at bits 8i + 2b (+ the row's colour parity).  A 3-agree
+// site flips iff its e0 bit is set, a 4-agree site iff its e0 and e1 bits
+// are.
 template <int CW, bool OBS, bool CG>
 __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundKeys& rk, const uint32_t* s_lut,
                                                uint64_t item, int lane, PhaseAcc& acc)
@@ -282,17 +290,16 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
         const uint64_t w = (uint64_t)it.y * a.W + (uint64_t)it.ch * CW + k;  // word index
         const uint64_t ctr = 4ull * w;                                      // 4w+q never carries into the high word
         const PhiloxChunk pc = philox_chunk((uint32_t)(ctr >> 32), a.sweep, a.colour + 2u, rk);
-        uint32_t e0 = 0, e1 = 0;
+        uint64_t e0 = 0, e1 = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)q, pc, rk);
-            const uint32_t j0 = lut_find(s_lut, r.x), j1 = lut_find(s_lut, r.y);
-            const uint32_t j2 = lut_find(s_lut, r.z), j3 = lut_find(s_lut, r.w);
-            const uint32_t nib = j0 | (j1 << 4) | (j2 << 8) | (j3 << 12);  // uniforms 4q .. 4q+3
-            if (q < 2) e0 |= nib << (16 * q);
-            else e1 |= nib << (16 * (q - 2));
+            const uint32_t b4 = lut_find_spread(s_lut, r.x) | (lut_find_spread(s_lut, r.y) << 8) |
+                                (lut_find_spread(s_lut, r.z) << 16) | (lut_find_spread(s_lut, r.w) << 24);
+            if (q < 2) e0 |= (uint64_t)b4 << (32 * q);  // uniforms 4q .. 4q+3
+            else e1 |= (uint64_t)b4 << (32 * (q - 2));
         }
-        const uint64_t x0 = spread_even(e0) << it.p, x1 = spread_even(e1) << it.p;
+        const uint64_t x0 = e0 << it.p, x1 = e1 << it.p;
         const uint64_t acc4 = it.u4[k] & x0, acc8 = it.u8[k] & x0 & x1;
         it.flip[k] |= acc4 | acc8;
         if constexpr (OBS) it.dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
