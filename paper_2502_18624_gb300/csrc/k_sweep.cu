@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_c
 }
 
 template <int CW, bool OBS>
-__global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
+__global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
 {
     __shared__ uint32_t s_lut[kLutSlots];
     if (threadIdx.x < kLutSlots) s_lut[threadIdx.x] = lut_slot(a.lut, threadIdx.x);
@@ -82,8 +82,11 @@ cudaError_t query_sweep_occupancy(LaunchShape& ls)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ls.ising_bpsm, k_ising_phase<2, true>, kSweepThreads, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ls.bc_bpsm, k_bc_phase<true>, kSweepThreads, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ls.lut_bpsm, k_ising_phase_lut<2, true>, kSweepThreads, 0);
     if (ls.ising_bpsm < 1) ls.ising_bpsm = 1;
     if (ls.bc_bpsm < 1) ls.bc_bpsm = 1;
+    if (ls.lut_bpsm < 1) ls.lut_bpsm = 1;
     return e;
 }
 
@@ -91,7 +94,7 @@ cudaError_t launch_ising_phase(const IsingPhaseArgs& a, const LaunchShape& ls, c
 {
     const bool even_words = (a.W % 2) == 0;
     const uint64_t nitems = (uint64_t)a.L * (even_words ? a.W / 2 : a.W);
-    const int grid = blocks_for(nitems, ls.sms, ls.ising_bpsm);
+    const int grid = blocks_for(nitems, ls.sms, a.rng == LAT_RNG_TABLE_MODE ? ls.lut_bpsm : ls.ising_bpsm);
     if (a.rng == LAT_RNG_TABLE_MODE) {
         if (even_words) {
             if (a.obs) k_ising_phase_lut<2, true><<<grid, kSweepThreads, 0, st>>>(a);

@@ -13,6 +13,7 @@ struct LaunchShape {
     int sms;          // multiprocessors on the device
     int ising_bpsm;   // resident blocks per SM of the sweep kernels
     int bc_bpsm;
+    int lut_bpsm;     // ... and of the lookup-table Ising kernel
 };
 
 // Sweep phases (k_sweep.cu).
