@@ -473,7 +473,7 @@ def served_bench(args):
         e.close()
     eng = serve.GpuEngine(args.max_batch, args.step_sweeps, tiles=tiles)
     srv = serve.Server(eng, mem_budget=int(args.mem_gib * (1 << 30)), max_batch=args.max_batch,
-                       step_updates=args.step_updates, max_step_sweeps=args.step_sweeps)
+                       step_updates=args.step_updates, max_step_sweeps=args.step_sweeps, policy=args.policy)
     sampler = ClockSampler(gpu_id_for(local)).start()
     barrier(dist, device)
     res = srv.run(jobs)
@@ -500,7 +500,7 @@ def served_bench(args):
                                        "Blume-Capel Delta in {0.5,1,1.5}, L=2^8..2^14, T=[0.7,1.3] Tc_ref, "
                                        "sweeps log-uniform 10..10000, C(r<=min(L/2,1024)) at sweeps 2^k), "
                                        "seed 20250" % (len(jobs), args.rate),
-                           "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch,
+                           "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch, "policy": args.policy,
                            "step_updates": args.step_updates, "parallelism": "replicas" if world > 1 else "single"},
                 "served": dict(s_srv, steps=srv.steps, peak_batch=srv.peak_batch, peak_mem=srv.peak_mem),
                 "sequential_plain": dict(s_seq, gpu_launches=seq_launches), "bit_exact": exact, "clocks": clocks,
@@ -559,6 +559,8 @@ def main(argv=None):
     ap.add_argument("--max-batch", type=int, default=256, help="served: most jobs resident at once")
     ap.add_argument("--step-updates", type=float, default=1e10, help="served: work per step (spin updates)")
     ap.add_argument("--step-sweeps", type=int, default=256, help="served: most sweeps per job per step")
+    ap.add_argument("--policy", choices=["fair", "srpt"], default="fair",
+                    help="served: per-step sweep plan (equal quotas, or shortest remaining work first)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="oracle CPU-baseline budget; 0 skips it (profiling runs)")
     ap.add_argument("--L", type=int, default=None, help="override the linear size (small profiling cases)")

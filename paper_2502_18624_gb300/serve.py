@@ -50,20 +50,34 @@ def next_measurement(done: int) -> int:
     return p
 
 
-def plan_step(active, budget_updates: float, max_sweeps: int):
+def plan_step(active, budget_updates: float, max_sweeps: int, policy: str = "fair"):
     """Sweeps per resident job for one step.
 
-    active: list of (L, sweeps_done, sweeps_total).  Every job gets the same
-    quota q = budget / sum(L^2) (at least 1), capped by max_sweeps, by its
-    remaining sweeps and by its next measurement point."""
+    active: list of (L, sweeps_done, sweeps_total).  A job's cap is the
+    smallest of max_sweeps, its remaining sweeps and the sweeps to its next
+    measurement point.
+      fair: every job gets the same quota q = budget / sum(L^2) (at least 1),
+            capped.
+      srpt: jobs are served in order of increasing remaining work
+            (L^2 x remaining sweeps); each takes its cap while the budget
+            lasts, and every job gets at least one sweep, so none starves."""
     if not active:
         return []
-    tot = float(sum(L * L for (L, _, _) in active))
-    q = int(max(1, min(max_sweeps, budget_updates // max(tot, 1.0))))
-    out = []
-    for (L, done, total) in active:
-        k = min(q, total - done, next_measurement(done) - done)
-        out.append(max(0, k))
+    caps = [max(0, min(max_sweeps, total - done, next_measurement(done) - done)) for (_, done, total) in active]
+    if policy == "fair":
+        tot = float(sum(L * L for (L, _, _) in active))
+        q = int(max(1, min(max_sweeps, budget_updates // max(tot, 1.0))))
+        return [min(q, c) for c in caps]
+    if policy != "srpt":
+        raise ValueError("unknown policy %r" % policy)
+    order = sorted(range(len(active)), key=lambda i: (active[i][0] ** 2 * (active[i][2] - active[i][1]), i))
+    out = [0] * len(active)
+    left = float(budget_updates)
+    for i in order:
+        L2 = float(active[i][0]) ** 2
+        k = min(caps[i], max(1, int(left // L2)))
+        out[i] = k
+        left -= k * L2
     return out
 
 
@@ -113,13 +127,14 @@ class GpuEngine:
 
 class Server:
     def __init__(self, engine, mem_budget: int, max_batch: int, step_updates: float = 2e9,
-                 max_step_sweeps: int = 256, clock=time.perf_counter, sleep=time.sleep):
+                 max_step_sweeps: int = 256, clock=time.perf_counter, sleep=time.sleep, policy: str = "fair"):
         self.engine = engine
         self.mem_budget = mem_budget
         self.max_batch = max_batch
         self.step_updates = step_updates
         self.max_step_sweeps = max_step_sweeps
         self.clock, self.sleep = clock, sleep
+        self.policy = policy
         self.steps = 0
         self.peak_mem = 0
         self.peak_batch = 0
@@ -158,7 +173,7 @@ class Server:
                 continue
             self.peak_batch = max(self.peak_batch, len(active))
             plan = plan_step([(a[0].job.L, a[2], a[0].job.sweeps) for a in active], self.step_updates,
-                             self.max_step_sweeps)
+                             self.max_step_sweeps, self.policy)
             obs = self.engine.advance([a[1] for a in active], plan)
             self.steps += 1
             keep = []

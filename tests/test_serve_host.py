@@ -132,3 +132,40 @@ def test_plan_step_shares_the_budget():
     ks = serve.plan_step([(1024, 64, 10**6 - 1), (2048, 64, 10**6 - 1)], budget_updates=1024**2 * 5 * 10,
                          max_sweeps=64)
     assert ks == [10, 10]
+
+
+def test_plan_step_srpt_serves_short_jobs_first():
+    # two big jobs and one small one; the budget covers the small job's cap and a few big sweeps
+    active = [(4096, 10, 1000), (256, 3, 50), (4096, 100, 5000)]
+    ks = serve.plan_step(active, budget_updates=4096**2 * 6 + 256**2, max_sweeps=64, policy="srpt")
+    assert ks[1] == 1                     # capped by its next measurement point (4)
+    assert ks[0] == 6 and ks[2] == 1      # the shorter big job takes the rest; the other keeps one sweep
+    fair = serve.plan_step(active, budget_updates=4096**2 * 6 + 256**2, max_sweeps=64, policy="fair")
+    assert fair == [2, 1, 2]             # q = floor(budget / sum L^2) = 2, capped
+    with pytest.raises(ValueError):
+        serve.plan_step(active, 1e9, 64, policy="lifo")
+
+
+@pytest.mark.parametrize("policy", ["fair", "srpt"])
+def test_both_policies_run_every_sweep_and_measurement(policy):
+    clock = Clock()
+    eng = FakeEngine(clock)
+    srv = serve.Server(eng, mem_budget=600_000, max_batch=16, step_updates=5e6, max_step_sweeps=64,
+                       clock=clock, sleep=clock.sleep, policy=policy)
+    res = srv.run(_jobs())
+    for r in res:
+        assert list(np.concatenate(r.obs)["sweep"]) == list(range(1, r.job.sweeps + 1))
+        assert sorted(r.corr) == [2 ** k for k in range(0, 20) if 2 ** k <= r.job.sweeps]
+        assert r.final_hash == r.job.id * 7 + r.job.sweeps
+    assert eng.live == 0
+
+
+def test_srpt_lowers_the_median_latency_of_a_burst():
+    lat = {}
+    for policy in ("fair", "srpt"):
+        clock = Clock()
+        srv = serve.Server(FakeEngine(clock), mem_budget=10**12, max_batch=256, step_updates=5e7, max_step_sweeps=256,
+                           clock=clock, sleep=clock.sleep, policy=policy)
+        res = srv.run(workloads.served_jobs(n=80, rate=1e6, seed=11, kmin=6, kmax=12, smin=10, smax=3000))
+        lat[policy] = np.median([r.latency for r in res])
+    assert lat["srpt"] < lat["fair"]
