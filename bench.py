@@ -558,8 +558,8 @@ def main(argv=None):
     ap.add_argument("--mem-gib", type=float, default=48.0, help="served: device memory budget")
     ap.add_argument("--max-batch", type=int, default=256, help="served: most jobs resident at once")
     ap.add_argument("--step-updates", type=float, default=1e10, help="served: work per step (spin updates)")
-    ap.add_argument("--step-sweeps", type=int, default=256, help="served: most sweeps per job per step")
-    ap.add_argument("--policy", choices=["fair", "srpt"], default="fair",
+    ap.add_argument("--step-sweeps", type=int, default=16, help="served: most sweeps per job per step")
+    ap.add_argument("--policy", choices=["fair", "srpt"], default="srpt",
                     help="served: per-step sweep plan (equal quotas, or shortest remaining work first)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="oracle CPU-baseline budget; 0 skips it (profiling runs)")

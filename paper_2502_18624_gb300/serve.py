@@ -126,8 +126,15 @@ class GpuEngine:
 
 
 class Server:
+    """Continuous batching: admits arriving jobs first-come-first-served while
+    their device footprint fits mem_budget (at most max_batch resident), and
+    advances every resident job in one engine step at a time.  The sweeps a
+    job gets per step come from plan_step (policy "srpt" or "fair", at most
+    max_step_sweeps); C(r) is measured after sweeps 1, 2, 4, ... and a job
+    leaves, freeing its memory, when its sweeps are done."""
+
     def __init__(self, engine, mem_budget: int, max_batch: int, step_updates: float = 2e9,
-                 max_step_sweeps: int = 256, clock=time.perf_counter, sleep=time.sleep, policy: str = "fair"):
+                 max_step_sweeps: int = 16, clock=time.perf_counter, sleep=time.sleep, policy: str = "srpt"):
         self.engine = engine
         self.mem_budget = mem_budget
         self.max_batch = max_batch
