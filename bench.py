@@ -263,6 +263,7 @@ def native(args, wl):
     max_secs = reduce_max(dist, secs, device)
     L2 = float(wl["L"]) ** 2
     value = whole_job(L2 * K, world, max_secs)
+    thresholds = [int(x) for x in lat.thresholds()]
     counts = lat.spin_counts()  # consistency check: every site holds a spin, L^2 in total
     assert counts[3] == 0 and int(counts[:3].sum()) == wl["L"] ** 2, "spin counts inconsistent: %s" % counts
     final_hash = lat.hash()
@@ -300,7 +301,7 @@ def native(args, wl):
                 "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "
                              "achieved counts 40 IMAD-ops per needed Philox block",
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
-    wl = dict(wl, corr_launches=corr_launches, corr_share=corr_s / max_secs)
+    wl = dict(wl, corr_launches=corr_launches, corr_share=corr_s / max_secs, thresholds=thresholds)
     return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist,
                   batched)
 
@@ -389,6 +390,7 @@ def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, rooflin
             "config": {"workload": wl["name"].replace("K sweeps", "%d sweeps" % K), "L": wl["L"], "T": wl["T"],
                        "Delta": wl["Delta"], "seed": wl["seed"], "rmax": wl["rmax"], "sweeps": K,
                        "correlation_points": ncorr, "correlation_share_of_time": wl.get("corr_share"),
+                       "thresholds": wl.get("thresholds"),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (packed lattice %d MiB vs 126 MiB L2), no flush" %
                              (L2 / 8 / (1 << 20) * (1 if wl["model"] == 0 else 2))},

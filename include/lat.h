@@ -326,7 +326,9 @@ int lat_runner_inject_stall(lat_runner_t* r, uint32_t index);
  * nsweeps[i] records) that receive the exact (M, B, Q) and draw count after
  * every sweep, as lat_sweep would.  The call first synchronises every
  * handle's own stream, and synchronises the runner's stream before it
- * returns.  Errors: LAT_EINVAL, LAT_ECUDA, LAT_ETIMEDOUT. */
+ * returns.  Errors: LAT_EINVAL, LAT_ECUDA, LAT_ETIMEDOUT, and LAT_ESTATE if
+ * the tile maps built on the host fail their consistency check (an internal
+ * error; nothing is launched). */
 int lat_runner_run(lat_runner_t* r, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
                    lat_obs* const* per_sweep);
 

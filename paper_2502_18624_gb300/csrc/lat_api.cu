@@ -189,6 +189,7 @@ int lat_lut_table(const lat_params* p, uint32_t out[16])
 
 int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, lat_t** out)
 {
+    const NvtxRange range("lat_create");
     if (!out || !params_ok(p)) return LAT_EINVAL;
     *out = nullptr;
     if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) % kAlign) != 0) return LAT_EINVAL;
@@ -235,6 +236,7 @@ int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, l
 
 int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
 {
+    const NvtxRange range("lat_sweep");
     if (!h) return LAT_EINVAL;
     if (h->next_sweep + nsweeps > kLastSweep) return LAT_EINVAL;
     const uint32_t L = h->p.L, W = h->W;
@@ -309,6 +311,7 @@ int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
 
 int lat_measure(lat_t* h, lat_obs* out)
 {
+    const NvtxRange range("lat_measure");
     if (!h || !out) return LAT_EINVAL;
     long long v[3];
     cudaError_t e = launch_measure(h->p.model, h->spins(), h->p.L, h->W, h->misc(), h->ls.sms, h->stream);
@@ -325,6 +328,7 @@ int lat_measure(lat_t* h, lat_obs* out)
 
 int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy)
 {
+    const NvtxRange range("lat_correlation");
     if (!h || !cx || !cy || rmax > h->p.L / 2) return LAT_EINVAL;
     long long* dcx = h->corr();
     long long* dcy = dcx + (rmax + 1);
@@ -339,6 +343,7 @@ int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy)
 
 int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr, int64_t* cx, int64_t* cy)
 {
+    const NvtxRange range("lat_correlation_sampled");
     if (!h || !valid_R(R) || (nr && (!r || !cx || !cy))) return LAT_EINVAL;
     for (uint32_t i = 0; i < nr; ++i)
         if (r[i] > h->p.L / 2) return LAT_EINVAL;
@@ -366,6 +371,7 @@ int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr
 int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uint32_t* n_out, uint32_t* r_out,
                              int64_t* cx, int64_t* cy, uint64_t* nsrc)
 {
+    const NvtxRange range("lat_correlation_protocol");
     if (!h || !n_out || !valid_R(R)) return LAT_EINVAL;
     const uint32_t L = h->p.L;
     const uint32_t rfull = std::min<uint32_t>(2 * R, L / 2);
@@ -388,6 +394,7 @@ int lat_correlation_protocol(lat_t* h, uint64_t t, uint32_t R, uint32_t cap, uin
 
 int lat_spin_counts(lat_t* h, int64_t counts[4])
 {
+    const NvtxRange range("lat_spin_counts");
     if (!h || !counts) return LAT_EINVAL;
     cudaError_t e = launch_spin_counts(h->p.model, h->spins(), h->p.L, h->W, h->misc() + 24, h->ls.sms, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(counts, h->misc() + 24, 4 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
@@ -397,6 +404,7 @@ int lat_spin_counts(lat_t* h, int64_t counts[4])
 
 int lat_sd_hist(lat_t* h, int64_t* hist)
 {
+    const NvtxRange range("lat_sd_hist");
     if (!h || !hist) return LAT_EINVAL;
     cudaError_t e = launch_sd_hist(h->p.model, h->spins(), h->p.L, h->W, h->misc() + 4, h->ls.sms, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hist, h->misc() + 4, 9 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);

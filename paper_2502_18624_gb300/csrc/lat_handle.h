@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lat.h"
 #include "lat_internal.cuh"
 
@@ -36,3 +38,12 @@ struct lat {
     uint32_t* rlist() const { return reinterpret_cast<uint32_t*>(buf + lay.rlist); }
 };
 
+// A named NVTX range over one entry point, so that profiler timelines show
+// the library's calls around their kernels (header-only NVTX3: no cost
+// beyond a pointer test when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};

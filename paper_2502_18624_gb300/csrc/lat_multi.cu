@@ -396,9 +396,34 @@ int lat_runner_inject_stall(lat_runner_t* R, uint32_t index)
     return LAT_OK;
 }
 
+// The maps the persistent kernel indexes with no check of its own: every
+// tile number g < total must resolve to a phase k (phase_base), a lattice
+// r < active[k] (tile_prefix) and a tile t < ntiles[r], and every tile must
+// cover items inside its lattice.  Built on the host from validated input,
+// so a failure here is an internal error (LAT_ESTATE), never a launch.
+static bool runner_maps_ok(const MultiDesc* hd, const uint32_t* htp, const unsigned long long* hpb,
+                           const uint32_t* hact, uint32_t n, uint32_t K)
+{
+    if (htp[0] != 0) return false;
+    for (uint32_t s = 0; s < n; ++s) {
+        const MultiDesc& d = hd[s];
+        if (d.tile_items == 0 || d.tile_items % kMultiThreads != 0 || d.ntiles == 0) return false;
+        if ((uint64_t)d.ntiles * d.tile_items < d.items || (uint64_t)(d.ntiles - 1) * d.tile_items >= d.items)
+            return false;
+        if (htp[s + 1] != htp[s] + d.ntiles) return false;
+    }
+    if (hpb[0] != 0) return false;
+    for (uint32_t k = 0; k < K; ++k) {
+        if (hact[k] == 0 || hact[k] > n || (k > 0 && hact[k] > hact[k - 1])) return false;
+        if (hpb[k + 1] != hpb[k] + htp[hact[k]]) return false;
+    }
+    return true;
+}
+
 int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
                    lat_obs* const* per_sweep)
 {
+    const NvtxRange range("lat_runner_run");
     if (!R || !lattices || !nsweeps || n == 0 || n > R->cap) return LAT_EINVAL;
     for (uint32_t i = 0; i < n; ++i) {
         if (!lattices[i] || nsweeps[i] > R->max_sweeps) return LAT_EINVAL;
@@ -496,6 +521,7 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
         base += htp[act];
     }
     hpb[K] = base;
+    if (!runner_maps_ok(hd, htp, hpb, hact, n, K)) return LAT_ESTATE;
     std::memset(hctl, 0, sizeof(MultiCtl));
     hctl->total = base;
     hctl->nphases = K;
