@@ -36,6 +36,8 @@ class JobResult:
     obs: list = field(default_factory=list)      # per-sweep record arrays, in order
     corr: dict = field(default_factory=dict)     # completed sweeps -> (cx, cy)
     final_hash: int = 0
+    status: str = "done"                         # "done", "failed" or "cancelled"
+    error: str = ""                              # why a job failed
 
     @property
     def latency(self) -> float:
@@ -121,6 +123,9 @@ class GpuEngine:
         h.close()
         return v
 
+    def abort(self, h) -> None:
+        h.close()
+
     def close(self):
         self.runner.close()
 
@@ -146,20 +151,56 @@ class Server:
         self.peak_mem = 0
         self.peak_batch = 0
 
-    def run(self, jobs):
+    def _release(self, h):
+        """Close a job's lattice without reading a result (failure or cancel)."""
+        abort = getattr(self.engine, "abort", None)
+        try:
+            if abort is not None:
+                abort(h)
+            else:
+                self.engine.finish(h)
+        except Exception:
+            pass
+
+    def run(self, jobs, cancels=None):
+        """Serve `jobs`; cancels maps a job id to the time (seconds after the
+        start) at which it is withdrawn, whether it is still waiting, running
+        or not yet arrived.  A job whose lattice cannot be created, or whose
+        step or measurement raises, ends with status "failed"; the other jobs
+        go on."""
         jobs = sorted(jobs, key=lambda j: (j.arrival, j.id))
         arrivals = deque(jobs)
         pending = deque()
         active = []  # [result, handle, done, footprint]
         results = {}
+        cancel_at = dict(cancels or {})
         used = 0
         t0 = self.clock()
+
+        def end(r, status, error=""):
+            r.status, r.error = status, error
+            r.completed = self.clock() - t0
+
         while arrivals or pending or active:
             now = self.clock() - t0
             while arrivals and arrivals[0].arrival <= now:
                 j = arrivals.popleft()
                 results[j.id] = JobResult(j)
                 pending.append(j)
+            # withdrawals
+            if cancel_at:
+                for j in [j for j in pending if cancel_at.get(j.id, float("inf")) <= now]:
+                    pending.remove(j)
+                    end(results[j.id], "cancelled")
+                keep = []
+                for a in active:
+                    if cancel_at.get(a[0].job.id, float("inf")) <= now:
+                        self._release(a[1])
+                        used -= a[3]
+                        end(a[0], "cancelled")
+                    else:
+                        keep.append(a)
+                active = keep
             # admission: first come, first served, by device footprint
             while pending and len(active) < self.max_batch:
                 j = pending[0]
@@ -169,11 +210,16 @@ class Server:
                 if used + fp > self.mem_budget:
                     break
                 pending.popleft()
-                used += fp
-                self.peak_mem = max(self.peak_mem, used)
                 r = results[j.id]
                 r.admitted = self.clock() - t0
-                active.append([r, self.engine.create(j), 0, fp])
+                try:
+                    h = self.engine.create(j)
+                except Exception as e:  # e.g. the device allocation failed
+                    end(r, "failed", repr(e))
+                    continue
+                used += fp
+                self.peak_mem = max(self.peak_mem, used)
+                active.append([r, h, 0, fp])
             if not active:
                 if arrivals:
                     self.sleep(max(0.0, arrivals[0].arrival - (self.clock() - t0)))
@@ -181,7 +227,16 @@ class Server:
             self.peak_batch = max(self.peak_batch, len(active))
             plan = plan_step([(a[0].job.L, a[2], a[0].job.sweeps) for a in active], self.step_updates,
                              self.max_step_sweeps, self.policy)
-            obs = self.engine.advance([a[1] for a in active], plan)
+            try:
+                obs = self.engine.advance([a[1] for a in active], plan)
+            except Exception as e:  # e.g. a device wait timed out: these lattices are in doubt
+                for a in active:
+                    self._release(a[1])
+                    used -= a[3]
+                    end(a[0], "failed", repr(e))
+                active = []
+                self.steps += 1
+                continue
             self.steps += 1
             keep = []
             for a, k, o in zip(active, plan, obs):
@@ -189,14 +244,20 @@ class Server:
                 if k:
                     r.obs.append(o)
                     a[2] += k
-                if a[2] > 0 and (a[2] & (a[2] - 1)) == 0 and a[2] not in r.corr:
-                    r.corr[a[2]] = self.engine.measure(h)
-                if a[2] >= r.job.sweeps:
-                    r.final_hash = self.engine.finish(h)
-                    r.completed = self.clock() - t0
+                try:
+                    if a[2] > 0 and (a[2] & (a[2] - 1)) == 0 and a[2] not in r.corr:
+                        r.corr[a[2]] = self.engine.measure(h)
+                    if a[2] >= r.job.sweeps:
+                        r.final_hash = self.engine.finish(h)
+                        end(r, "done")
+                        used -= a[3]
+                        continue
+                except Exception as e:
+                    self._release(h)
                     used -= a[3]
-                else:
-                    keep.append(a)
+                    end(r, "failed", repr(e))
+                    continue
+                keep.append(a)
             active = keep
         self.wall = self.clock() - t0
         return [results[j.id] for j in jobs]
@@ -228,11 +289,18 @@ def run_sequential(engine, jobs, clock=time.perf_counter, sleep=time.sleep):
 
 
 def summarize(results, wall: float) -> dict:
-    lat = np.array([r.latency for r in results])
-    updates = float(sum(r.job.L * r.job.L * r.job.sweeps for r in results))
-    return {"jobs": len(results), "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "wall_s": wall,
-            "updates": updates, "flips_per_ns": updates / wall / 1e9}
+    """Latency and throughput over the jobs that completed; counts of the others."""
+    done = [r for r in results if r.status == "done"]
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    updates = float(sum(r.job.L * r.job.L * r.job.sweeps for r in done))
+    out = {"jobs": len(results), "p50_latency_s": float(np.percentile(lat, 50)),
+           "p99_latency_s": float(np.percentile(lat, 99)), "wall_s": wall,
+           "updates": updates, "flips_per_ns": updates / wall / 1e9}
+    for status in ("failed", "cancelled"):
+        n = sum(1 for r in results if r.status == status)
+        if n:
+            out[status] = n
+    return out
 
 
 def same_results(a: JobResult, b: JobResult) -> bool:

@@ -169,3 +169,83 @@ def test_srpt_lowers_the_median_latency_of_a_burst():
         res = srv.run(workloads.served_jobs(n=80, rate=1e6, seed=11, kmin=6, kmax=12, smin=10, smax=3000))
         lat[policy] = np.median([r.latency for r in res])
     assert lat["srpt"] < lat["fair"]
+
+
+class FlakyEngine(FakeEngine):
+    """Fails the creation of some jobs, and one whole step."""
+
+    def __init__(self, clock, bad_create=(), bad_step=None):
+        super().__init__(clock)
+        self.bad_create, self.bad_step, self.nsteps, self.aborted = set(bad_create), bad_step, 0, []
+
+    def create(self, job):
+        if job.id in self.bad_create:
+            raise MemoryError("device allocation failed for job %d" % job.id)
+        return super().create(job)
+
+    def advance(self, handles, nsweeps):
+        self.nsteps += 1
+        if self.nsteps == self.bad_step:
+            raise RuntimeError("lat_runner_run failed: a bounded device-side wait gave up (-4)")
+        return super().advance(handles, nsweeps)
+
+    def abort(self, h):
+        h.closed = True
+        self.live -= self.footprint(h.job)
+        self.aborted.append(h.job.id)
+
+
+def _check_done(r):
+    assert list(np.concatenate(r.obs)["sweep"]) == list(range(1, r.job.sweeps + 1))
+    assert r.final_hash == r.job.id * 7 + r.job.sweeps
+
+
+def test_failed_admission_fails_only_that_job():
+    clock = Clock()
+    jobs = _jobs(30, 4)
+    bad = {jobs[3].id, jobs[10].id}
+    eng = FlakyEngine(clock, bad_create=bad)
+    res = serve.Server(eng, mem_budget=600_000, max_batch=16, step_updates=5e6, max_step_sweeps=64,
+                       clock=clock, sleep=clock.sleep).run(jobs)
+    for r in res:
+        if r.job.id in bad:
+            assert r.status == "failed" and "allocation" in r.error and not r.obs
+        else:
+            assert r.status == "done"
+            _check_done(r)
+    assert eng.live == 0
+    s = serve.summarize(res, 1.0)
+    assert s["failed"] == 2 and s["jobs"] == 30
+
+
+def test_failed_step_fails_its_jobs_and_the_rest_go_on():
+    clock = Clock()
+    jobs = _jobs(40, 6)
+    eng = FlakyEngine(clock, bad_step=5)
+    res = serve.Server(eng, mem_budget=600_000, max_batch=8, step_updates=5e6, max_step_sweeps=16,
+                       clock=clock, sleep=clock.sleep).run(jobs)
+    failed = [r for r in res if r.status == "failed"]
+    assert failed and all("wait gave up" in r.error for r in failed)
+    assert sorted(r.job.id for r in failed) == sorted(eng.aborted)
+    for r in res:
+        if r.status == "done":
+            _check_done(r)
+    assert sum(r.status == "done" for r in res) == len(jobs) - len(failed)
+    assert eng.live == 0
+
+
+def test_cancellation_while_waiting_running_or_before_arrival():
+    clock = Clock()
+    jobs = _jobs(30, 8)
+    first, late = jobs[0], jobs[-1]
+    eng = FlakyEngine(clock)
+    srv = serve.Server(eng, mem_budget=300_000, max_batch=4, step_updates=5e6, max_step_sweeps=8,
+                       clock=clock, sleep=clock.sleep)
+    res = srv.run(jobs, cancels={first.id: first.arrival + 1e-6, late.id: 0.0})
+    by = {r.job.id: r for r in res}
+    assert by[first.id].status == "cancelled" and by[late.id].status == "cancelled" and not by[late.id].obs
+    for r in res:
+        if r.job.id not in (first.id, late.id):
+            assert r.status == "done"
+            _check_done(r)
+    assert eng.live == 0
