@@ -306,3 +306,35 @@ def test_empty_calls_change_nothing(gpu, model):
     r.close()
     assert lat.hash() == h0 and lat.sweep_index == t0
     lat.close()
+
+
+def _phase_rule(s, colour, flip_if_agree_at_most):
+    """One colour phase of a deterministic Ising rule, in numpy."""
+    L = s.shape[0]
+    y, x = np.indices((L, L))
+    agree = sum((np.roll(s, d, axis=a) == s).astype(int) for a in (0, 1) for d in (1, -1))
+    act = ((x + y) % 2 == colour) & (agree <= flip_if_agree_at_most)
+    return np.where(act, -s, s).astype(np.int8)
+
+
+@pytest.mark.parametrize("L", [64, 192])
+def test_ising_zero_and_infinite_temperature_rules(gpu, L):
+    """Textbook limits of the Metropolis rule, independent of the oracle:
+    at T -> 0 a site flips iff at most two of its four neighbours agree with
+    it (dE = 2Js*h <= 0), which exercises every one of the 16 neighbour
+    patterns of the kernel's classification; at T -> infinity every site
+    flips, so one sweep negates the lattice."""
+    cold = b.Lattice(0, L, 1e-6, 5)
+    s = cold.spins()
+    for _ in range(3):
+        s = _phase_rule(_phase_rule(s, 0, 2), 1, 2)
+        obs = cold.sweep(1)
+        assert np.array_equal(cold.spins(), s)
+        assert int(obs["draws"][0]) == 0  # thresholds 0: no site draws
+    cold.close()
+    hot = b.Lattice(0, L, 1e15, 6)
+    s = hot.spins()
+    obs = hot.sweep(1)
+    # at T = 1e15 the bound is 2^32 - 1, not 2^32: uphill sites still draw, and this seed's draws all accept
+    assert np.array_equal(hot.spins(), -s) and int(obs["draws"][0]) > 0
+    hot.close()
