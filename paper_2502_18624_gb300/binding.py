@@ -442,6 +442,7 @@ class Runner:
         if getattr(self, "handle", None):
             lat_runner_destroy(self.handle)
             self.handle = None
+        self.buffer = None  # the device buffer goes back to torch's allocator
 
     def __enter__(self):
         return self
