@@ -6,8 +6,9 @@ for R >= 16 and direct lattice reads below), ragged source rows (L/R not a
 multiple of 64), repeats and arbitrary order in the distance list, and both
 models.  At full size (L = 2^17 Ising, 2^16 Blume-Capel) the lattice is a
 periodic tiling of a random tile, so every sum is (L/P)^2 times the oracle's
-sum on the tile; a swept full-size lattice checks R = 1 against the
-all-sites kernel.
+sum on the tile; the same tiling checks the bench's all-sites C(r <= 1024)
+element by element at full size, and a swept full-size lattice checks R = 1
+against the all-sites kernel.
 """
 import numpy as np
 import pytest
@@ -85,7 +86,6 @@ def _tiled_state(model, L, tile):
     """Packed device state of the lattice that repeats `tile` (P x P) in both axes."""
     P = tile.shape[0]
     big_row = np.tile(tile, (1, L // P))              # P x L int8
-    words = []
     bits = lambda m: np.packbits(m.astype(np.uint8), axis=1, bitorder="little").view(np.uint64)
     if model == 0:
         rows = bits(big_row == 1)                     # P x W
@@ -131,4 +131,23 @@ def test_full_size_swept_R1_equals_all_sites(gpu):
     assert np.array_equal(cx, fx) and np.array_equal(cy, fy)
     M, B, Q, _ = lat.measure()
     assert cx[1] + cy[1] == B
+    lat.close()
+
+
+@pytest.mark.parametrize("model,L,rmax", [(0, 1 << 17, 1024), (1, 1 << 16, 512)])
+def test_full_size_all_sites_correlation_tiled(gpu, orc, model, L, rmax):
+    """The bench's C(r) from every site, at its full size and rmax, element by
+    element: on a periodic tiling of a P x P tile every sum is (L/P)^2 times
+    the oracle's sum on the tile (distances taken on the tile's torus)."""
+    P = 256
+    rng = np.random.default_rng(9 + model)
+    vals = np.array([-1, 1] if model == 0 else [-1, 0, 1], dtype=np.int8)
+    tile = vals[rng.integers(0, vals.size, size=(P, P))]
+    T, Delta = (TC, 0.0) if model == 0 else (1.398, 1.0)
+    lat = b.Lattice(model, L, T, 3, Delta=Delta)
+    lat.set_state(_tiled_state(model, L, tile))
+    cx, cy = lat.correlation(rmax)
+    ox, oy = orc.correlation(tile, rmax)
+    k = (L // P) ** 2
+    assert np.array_equal(cx, k * ox) and np.array_equal(cy, k * oy)
     lat.close()
