@@ -150,4 +150,8 @@ def test_full_size_all_sites_correlation_tiled(gpu, orc, model, L, rmax):
     ox, oy = orc.correlation(tile, rmax)
     k = (L // P) ** 2
     assert np.array_equal(cx, k * ox) and np.array_equal(cy, k * oy)
+    # the separate (M, B, Q) reduction and the spin counts scale the same way
+    M, B, Q = orc.measure(model, tile)
+    assert lat.measure()[:3] == (k * M, k * B, k * Q)
+    assert lat.spin_counts().tolist() == [k * int((tile == v).sum()) for v in (-1, 0, 1)] + [0]
     lat.close()
