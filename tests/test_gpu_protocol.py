@@ -154,4 +154,5 @@ def test_full_size_all_sites_correlation_tiled(gpu, orc, model, L, rmax):
     M, B, Q = orc.measure(model, tile)
     assert lat.measure()[:3] == (k * M, k * B, k * Q)
     assert lat.spin_counts().tolist() == [k * int((tile == v).sum()) for v in (-1, 0, 1)] + [0]
+    assert np.array_equal(lat.sd_hist(), k * orc.sd_hist(tile))
     lat.close()
