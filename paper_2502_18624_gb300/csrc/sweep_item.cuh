@@ -1,6 +1,6 @@
 // sweep_item.cuh -- the update of one work item of a checkerboard colour
 // phase (section 3.1), shared by the one-lattice kernels (k_sweep.cu) and the
-// persistent multi-lattice kernel (k_multi.cu), so that both produce the same
+// persistent multi-lattice kernel (k_multi in lat_multi.cu), so that both produce the same
 // bits from the same counters.
 //
 // Layout: row-major, W = L/64 words per row; bit b of word (y, j) is site
