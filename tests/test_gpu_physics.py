@@ -86,3 +86,19 @@ def test_draw_count_equals_uphill_sites(gpu, orc):
         mid[(x + y) % 2 == 0] = s[(x + y) % 2 == 0]
         assert int(obs["draws"][0]) == _uphill(before, 0) + _uphill(mid, 1)
     lat.close()
+
+
+def test_sd_deviation_after_128_sweeps_within_the_papers_figure(gpu, orc):
+    """The paper prints the Schwinger-Dyson deviation after 128 steps at Tc
+    (tests/golden/sd_deviation_128_steps.json).  On L = 2^17 from a random
+    start the Ising deviation must not exceed it."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sd_deviation_128_steps.json")) as f:
+        golden = json.load(f)
+    L = 1 << 17
+    lat = b.Lattice(0, L, b.TC_ISING, 7)
+    lat.sweep(golden["steps"], record=False)
+    dev = abs(orc.sd_value(lat.sd_hist(), 1.0, b.TC_ISING) - 1.0)
+    lat.close()
+    assert dev <= golden["ising_at_Tc"], dev
