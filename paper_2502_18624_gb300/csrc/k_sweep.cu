@@ -19,7 +19,7 @@ namespace {
 constexpr int kSweepThreads = 256;
 
 template <int CW, bool OBS>
-__global__ void __launch_bounds__(kSweepThreads, 4) k_ising_phase(const __grid_constant__ IsingPhaseArgs a)
+__global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase(const __grid_constant__ IsingPhaseArgs a)
 {
     const IsingPhase ph{a.spins, a.L, a.W, a.sweep, a.colour, a.thr4, a.thr8, a.mode4, a.mode8};
     const uint64_t nitems = (uint64_t)a.L * (a.W / CW);
