@@ -40,9 +40,12 @@
  *   or_sweep_lut       Kaufman's exact finite-torus energy and Onsager's
  *                      energy reproduced by long runs; frequencies of the
  *                      generated bits; +-flip symmetry.
- *   or_pack/or_hash    numpy.packbits for the packing; the mixing function is
- *                      a fixed bijection, so the hash is "parity unpinned"
- *                      beyond the packing (it only compares two lattices).
+ *   or_pack            numpy.packbits (tests/test_oracle_measure.py).
+ *   or_hash_words/or_hash  every one-bit change of every canonical word and
+ *                      every exchange of two unequal words changes the hash;
+ *                      the Blume-Capel planes are not interchangeable; the
+ *                      mixer's avalanche (each input bit flips each output bit
+ *                      with frequency near 1/2) (tests/test_oracle_hash.py).
  */
 #include <math.h>
 #include <stdint.h>

@@ -124,6 +124,29 @@ def _sampled_fails(orc):
     return not (np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]))
 
 
+def _fails(fn, *a):
+    try:
+        fn(*a)
+    except AssertionError:
+        return True
+    return False
+
+
+def _hash_position_fails(orc):
+    import test_oracle_hash as th
+    return _fails(th.test_exchanging_two_unequal_words_changes_the_hash, orc, 0)
+
+
+def _hash_avalanche_fails(orc):
+    import test_oracle_hash as th
+    return _fails(th.test_mixer_avalanche, orc)
+
+
+def _pack_planes_fail(orc):
+    import test_oracle_measure as tm
+    return _fails(tm.test_pack_matches_packbits, orc, 1, 64)
+
+
 MUTATIONS = [
     ("sweep drops the east neighbour",
      "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
@@ -166,6 +189,14 @@ MUTATIONS = [
      "            for (uint64_t x = 0; x < L; x += R) {\n                int v = s[y * L + x];\n                ax += v * s[y * L + (x + r[i]) % L];",
      "            for (uint64_t x = 0; x < L; x += 1) {\n                int v = s[y * L + x];\n                ax += v * s[y * L + (x + r[i]) % L];",
      _sampled_fails),
+    ("hash blind to word positions (i ^ dropped)", "h += or_mix64(i ^ words[i]);", "h += or_mix64(words[i]);",
+     _hash_position_fails),
+    ("hash mixer missing its second multiply", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;",
+     "z = (z ^ (z >> 27));", _hash_avalanche_fails),
+    ("Blume-Capel planes swapped in the canonical packing",
+     "                if (v != 0) words[i] |= bit;\n                if (v == -1) words[n + i] |= bit;",
+     "                if (v != 0) words[n + i] |= bit;\n                if (v == -1) words[i] |= bit;",
+     _pack_planes_fail),
 ]
 
 
