@@ -319,6 +319,15 @@ int lat_runner_set_timeout(lat_runner_t* r, uint64_t ns);
  * index = 0xFFFFFFFF switches this off (the default). */
 int lat_runner_inject_stall(lat_runner_t* r, uint32_t index);
 
+/* Boundary testing: the per-lattice tile counters of later runs start at
+ * base instead of 0.  Inside a run the counter of a lattice with ntiles tiles
+ * per phase counts up to base + 2 * nsweeps * ntiles; a run in which that
+ * would reach 2^64 - 1 is rejected with LAT_EINVAL before anything is
+ * launched.  With base just below 2^32 a test crosses the 32-bit boundary in
+ * a few phases.  Results do not depend on base.  LAT_EINVAL for
+ * base = 2^64 - 1. */
+int lat_runner_set_counter_base(lat_runner_t* r, uint64_t base);
+
 /* Advance lattices[i] by nsweeps[i] sweeps (0 allowed), all in one launch
  * on the runner's stream.  1 <= n <= max_lattices, nsweeps[i] <=
  * max_sweeps, each handle at most once, Ising and Blume-Capel L <= 2^19.
@@ -326,7 +335,8 @@ int lat_runner_inject_stall(lat_runner_t* r, uint32_t index);
  * nsweeps[i] records) that receive the exact (M, B, Q) and draw count after
  * every sweep, as lat_sweep would.  The call first synchronises every
  * handle's own stream, and synchronises the runner's stream before it
- * returns.  Errors: LAT_EINVAL, LAT_ECUDA, LAT_ETIMEDOUT, and LAT_ESTATE if
+ * returns.  Errors: LAT_EINVAL (including a run whose tile counters would
+ * not fit, see lat_runner_set_counter_base), LAT_ECUDA, LAT_ETIMEDOUT, and LAT_ESTATE if
  * the tile maps built on the host fail their consistency check (an internal
  * error; nothing is launched). */
 int lat_runner_run(lat_runner_t* r, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
@@ -346,7 +356,8 @@ int lat_runner_destroy(lat_runner_t* r);
  *   model, L   as in lat_params (L a multiple of 64 within the same limits).
  *   dev_spins  device pointer to a packed lattice in the layout of
  *              lat_get_state (lat_create places it at the start of the
- *              caller's dev_buf); read only.
+ *              caller's dev_buf); read only; 16-byte aligned (LAT_EINVAL
+ *              otherwise, checked before anything is launched).
  *   rmax       0 <= rmax <= min(L/2, LAT_STATIC_RMAX); larger values give
  *              LAT_EINVAL.
  *   cx, cy     host arrays of rmax+1 entries, filled exactly as by
@@ -356,8 +367,10 @@ int lat_runner_destroy(lat_runner_t* r);
  * Scratch: a fixed file-scope device array of 2*(LAT_STATIC_RMAX+1) int64
  * (64 KiB) that every GPU loading the library keeps until the process
  * exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the array (it is cleared on
+ * (cudaGetSymbolAddress) with the device current and keeps it for the rest of
+ * the process; make that first call before any stream capture, and make no
+ * call after a cudaDeviceReset (the kept address belonged to the context
+ * that the reset ended).  All calls share the array (it is cleared on
  * the stream before each use), so calls whose work overlaps on the GPU race.
  * Calls no cudaMalloc, cudaFree or other allocating routine.
  * Errors: LAT_EINVAL (bad arguments), LAT_ECUDA. */

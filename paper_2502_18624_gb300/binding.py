@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         "lat_runner_run": (i32, [P, P, u32, P, P]),
         "lat_runner_destroy": (i32, [P]),
         "lat_runner_inject_stall": (i32, [P, u32]),
+        "lat_runner_set_counter_base": (i32, [P, u64]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -406,6 +407,10 @@ def lat_runner_inject_stall(r, index: int) -> None:
     _check(load().lat_runner_inject_stall(r, index), "lat_runner_inject_stall")
 
 
+def lat_runner_set_counter_base(r, base: int) -> None:
+    _check(load().lat_runner_set_counter_base(r, base), "lat_runner_set_counter_base")
+
+
 def lat_runner_destroy(r) -> None:
     _check(load().lat_runner_destroy(r), "lat_runner_destroy")
 
@@ -434,6 +439,9 @@ class Runner:
 
     def inject_stall(self, index: int) -> None:
         lat_runner_inject_stall(self.handle, index)
+
+    def set_counter_base(self, base: int) -> None:
+        lat_runner_set_counter_base(self.handle, base)
 
     def run(self, lattices, nsweeps, record: bool = True):
         return lat_runner_run(self.handle, [lt.handle for lt in lattices], nsweeps, record)

@@ -9,7 +9,10 @@
 // atomic counter hands tiles out in this order.  Before a block works on a
 // tile of (r, k > 0) it waits until every tile of (r, k-1) is done, counted
 // by done[r]; after the tile it publishes its stores (fence) and increments
-// done[r].
+// done[r].  done[r] is a 64-bit count that starts at a per-run base (0 unless
+// a test sets it): it reaches base + 2 * nsweeps * ntiles, which a 32-bit
+// count would not hold for large lattices with small tiles, and the host
+// checks that it fits before launching (runner_bounds.h).
 //
 // Progress.  A block waits only for tiles with smaller numbers, which were
 // taken by blocks that were already running, and those wait only for tiles
@@ -37,6 +40,7 @@
 #include <vector>
 
 #include "lat_handle.h"
+#include "runner_bounds.h"
 #include "sweep_item.cuh"
 
 using namespace latk;
@@ -69,6 +73,7 @@ struct MultiCtl {
     unsigned long long next;     // next tile number
     unsigned long long total;    // number of tiles
     unsigned long long timeout_ns;
+    unsigned long long done_base;  // value every done[] counter starts the run at
     unsigned int nphases;        // phases of the longest lattice
     unsigned int error;          // 0 ok, 1 a wait timed out
     unsigned int err_lattice, err_phase;
@@ -82,10 +87,10 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-__device__ __forceinline__ unsigned int load_acquire(const unsigned int* p)
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -127,7 +132,7 @@ template <int MINB>
 __global__ void __launch_bounds__(kMultiThreads, MINB)
     k_multi(const MultiDesc* __restrict__ desc, const uint32_t* __restrict__ tile_prefix,
             const unsigned long long* __restrict__ phase_base, const uint32_t* __restrict__ active,
-            unsigned int* done, MultiCtl* ctl)
+            unsigned long long* done, MultiCtl* ctl)
 {
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
@@ -162,7 +167,8 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
         if (threadIdx.x == 0) {
             int stop = 0;
             if (k > 0) {
-                const unsigned int target = r == ctl->stall_lattice ? 0xFFFFFFFFu : k * d.ntiles;
+                const unsigned long long target = r == ctl->stall_lattice
+                    ? kRunnerStallTarget : ctl->done_base + (unsigned long long)k * d.ntiles;
                 const unsigned long long t0 = global_ns();
                 while (load_acquire(&done[r]) < target) {
                     if (*(volatile unsigned int*)&ctl->error) {
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
         flush_acc(colour ? rec : nullptr, rec ? rec + kObsDraws : nullptr, acc);
         __threadfence();  // this thread's lattice stores before the tile is published
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&done[r], 1u);
+        if (threadIdx.x == 0) atomicAdd(&done[r], 1ull);
     }
 }
 
@@ -227,7 +233,7 @@ RunnerLayout runner_layout(uint32_t cap, uint32_t max_sweeps)
     l.active = off;
     off = align_up(off + 2 * (size_t)max_sweeps * sizeof(uint32_t));
     l.done = off;
-    off = align_up(off + (size_t)cap * sizeof(unsigned int));
+    off = align_up(off + (size_t)cap * sizeof(unsigned long long));
     l.ctl = off;
     off = align_up(off + sizeof(MultiCtl));
     l.obs = off;
@@ -250,6 +256,7 @@ struct lat_runner {
     int minb;  // resident blocks per SM the persistent kernel is built for (2 or 3)
     unsigned long long timeout_ns;
     uint32_t stall;  // input index whose waits never complete (failure-path tests), or ~0
+    unsigned long long done_base;  // start value of the tile counters (0; tests move it near 2^32)
     std::map<std::pair<int, uint32_t>, uint32_t> tile_of;  // (model, L) -> items per tile
     // pinned host staging
     char* host;
@@ -261,7 +268,7 @@ struct lat_runner {
     uint32_t* d_tile_prefix() const { return reinterpret_cast<uint32_t*>(buf + lay.tile_prefix); }
     unsigned long long* d_phase_base() const { return reinterpret_cast<unsigned long long*>(buf + lay.phase_base); }
     uint32_t* d_active() const { return reinterpret_cast<uint32_t*>(buf + lay.active); }
-    unsigned int* d_done() const { return reinterpret_cast<unsigned int*>(buf + lay.done); }
+    unsigned long long* d_done() const { return reinterpret_cast<unsigned long long*>(buf + lay.done); }
     MultiCtl* d_ctl() const { return reinterpret_cast<MultiCtl*>(buf + lay.ctl); }
     long long* d_obs() const { return reinterpret_cast<long long*>(buf + lay.obs); }
     unsigned long long* d_bcthr() const { return reinterpret_cast<unsigned long long*>(buf + lay.bcthr); }
@@ -269,20 +276,20 @@ struct lat_runner {
 
 namespace {
 
-// Host staging layout (pinned): descriptors, tile prefix, phase base, active counts, control.
+// Host staging layout (pinned): descriptors, tile prefix, phase base, active
+// counts, control, tables, start values of the tile counters, records.
 size_t host_bytes_for(uint32_t cap, uint32_t max_sweeps)
 {
     return (size_t)cap * sizeof(MultiDesc) + ((size_t)cap + 1) * sizeof(uint32_t) +
+           (size_t)cap * sizeof(unsigned long long) +
            (2 * (size_t)max_sweeps + 1) * sizeof(unsigned long long) + 2 * (size_t)max_sweeps * sizeof(uint32_t) +
            sizeof(MultiCtl) + (size_t)cap * 54 * sizeof(unsigned long long) + 64 + 256 +
            (size_t)cap * max_sweeps * kObsWords * sizeof(long long);
 }
 
-cudaError_t enqueue_run(lat_runner* R, cudaStream_t st, uint32_t n)
+// The persistent launch itself (the tile counters are set by each run's uploads).
+cudaError_t enqueue_run(lat_runner* R, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(R->d_done(), 0, (size_t)R->cap * sizeof(unsigned int), st);
-    if (e != cudaSuccess) return e;
-    (void)n;
     if (R->minb == 3)
         k_multi<3><<<R->grid, kMultiThreads, 0, st>>>(R->d_desc(), R->d_tile_prefix(), R->d_phase_base(),
                                                       R->d_active(), R->d_done(), R->d_ctl());
@@ -330,6 +337,7 @@ int lat_runner_create(uint32_t max_lattices, uint32_t max_sweeps, void* dev_buf,
     R->minb = minb;
     R->timeout_ns = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
     R->stall = 0xFFFFFFFFu;
+    R->done_base = 0;
     R->have_graph = false;
     if (dev_buf) {
         if (bytes < R->lay.total) {
@@ -359,7 +367,7 @@ int lat_runner_create(uint32_t max_lattices, uint32_t max_sweeps, void* dev_buf,
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            const cudaError_t e1 = enqueue_run(R, cs, max_lattices);
+            const cudaError_t e1 = enqueue_run(R, cs);
             const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
                 cudaGraphInstantiate(&R->graph, g, 0) == cudaSuccess)
@@ -393,6 +401,13 @@ int lat_runner_inject_stall(lat_runner_t* R, uint32_t index)
 {
     if (!R) return LAT_EINVAL;
     R->stall = index;
+    return LAT_OK;
+}
+
+int lat_runner_set_counter_base(lat_runner_t* R, uint64_t base)
+{
+    if (!R || base >= kRunnerStallTarget) return LAT_EINVAL;
+    R->done_base = base;
     return LAT_OK;
 }
 
@@ -454,6 +469,8 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     hp += sizeof(MultiCtl);
     unsigned long long* hthr = reinterpret_cast<unsigned long long*>(hp);
     hp += (size_t)R->cap * 54 * sizeof(unsigned long long);
+    unsigned long long* hdone = reinterpret_cast<unsigned long long*>(hp);
+    hp += (size_t)R->cap * sizeof(unsigned long long);
     long long* hobs = reinterpret_cast<long long*>(R->host + (((size_t)(hp - R->host) + 255) / 256 * 256));
 
     // The sparsest phase of lattice order[s] is its last one, where only the
@@ -492,6 +509,7 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
         if (tile > d.items) tile = (d.items + kMultiThreads - 1) / kMultiThreads * kMultiThreads;
         d.tile_items = tile;
         d.ntiles = (d.items + tile - 1) / tile;
+        if (!runner_counts_fit(R->done_base, nsweeps[i], d.ntiles)) return LAT_EINVAL;
         d.sweep0 = (uint32_t)h->next_sweep;
         d.rk = h->rk;
         if (h->p.model == LAT_ISING) {
@@ -527,6 +545,8 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     hctl->nphases = K;
     hctl->timeout_ns = R->timeout_ns;
     hctl->stall_lattice = 0xFFFFFFFFu;
+    hctl->done_base = R->done_base;
+    for (uint32_t s = 0; s < n; ++s) hdone[s] = R->done_base;
     for (uint32_t s = 0; s < n; ++s)
         if (order[s] == R->stall) hctl->stall_lattice = s;
 
@@ -541,10 +561,11 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     up(R->lay.active, hact, (size_t)K * sizeof(uint32_t));
     up(R->lay.ctl, hctl, sizeof(MultiCtl));
     up(R->lay.bcthr, hthr, (size_t)n * 54 * sizeof(unsigned long long));
+    up(R->lay.done, hdone, (size_t)n * sizeof(unsigned long long));
     // per-sweep records of the lattices in this run start at zero (one contiguous region)
     const size_t obs_words = (size_t)n * R->max_sweeps * kObsWords;
     if (e == cudaSuccess && maxs > 0) e = cudaMemsetAsync(R->d_obs(), 0, obs_words * sizeof(long long), st);
-    if (e == cudaSuccess && K > 0) e = R->have_graph ? cudaGraphLaunch(R->graph, st) : enqueue_run(R, st, n);
+    if (e == cudaSuccess && K > 0) e = R->have_graph ? cudaGraphLaunch(R->graph, st) : enqueue_run(R, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hctl, R->d_ctl(), sizeof(MultiCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return LAT_ECUDA;

@@ -5,7 +5,10 @@ lattice advanced alone by lat_sweep, with identical per-sweep (M, B, Q) and
 draw counts, for a mix of models, sizes (ragged word counts included),
 temperatures (every acceptance mode) and sweep counts (zero included), over
 chained runs and any tile schedule.  A wait that runs out must come back as
-LAT_ETIMEDOUT and leave the runner usable.
+LAT_ETIMEDOUT and leave the runner usable.  The per-lattice tile counters
+are 64-bit: started just below 2^32 they cross it inside a run with no
+effect on any result, and a run whose counts could not fit is refused before
+anything is launched.
 """
 import numpy as np
 import pytest
@@ -32,7 +35,7 @@ def _check_same(run_lats, ref_lats, obs, ref_obs):
     for i, (a, r) in enumerate(zip(run_lats, ref_lats)):
         assert a.sweep_index == r.sweep_index, i
         assert a.hash() == r.hash(), "lattice %d differs" % i
-        if a.L <= 512:
+        if a.L <= 2048:
             assert np.array_equal(a.spins(), r.spins()), i
         assert np.array_equal(obs[i], ref_obs[i]), "per-sweep records of lattice %d differ" % i
 
@@ -105,5 +108,36 @@ def test_runner_on_the_batched_workload_sample(gpu):
     runner = b.Runner(len(pick), 32)
     obs = runner.run(lats, [20] * len(pick))
     ref_obs = [r.sweep(20) for r in refs]
+    _check_same(lats, refs, obs, ref_obs)
+    runner.close()
+
+
+def test_runner_counters_cross_the_32_bit_boundary(gpu):
+    jobs = [(0, 1024, TC, 0.0, 41), (1, 512, 1.4, 1.0, 42), (0, 2048, 0.9 * TC, 0.0, 43), (0, 192, TC, 0.0, 44)]
+    ns = [9, 6, 7, 5]
+    runner = b.Runner(4, 16)
+    for (m, L, _, _, _) in jobs:
+        runner.set_tile(m, L, 256)          # many tiles per phase, so the counts move fast
+    runner.set_counter_base((1 << 32) - 3)  # every counter passes 2^32 within its first phase
+    lats, refs = _make(jobs), _make(jobs)
+    obs = runner.run(lats, ns)
+    ref_obs = [r.sweep(k) for r, k in zip(refs, ns)]
+    _check_same(lats, refs, obs, ref_obs)
+    # a second run continues from the same base, chained on the same lattices
+    obs = runner.run(lats, [3, 4, 2, 6])
+    ref_obs = [r.sweep(k) for r, k in zip(refs, [3, 4, 2, 6])]
+    _check_same(lats, refs, obs, ref_obs)
+    # counts that would reach 2^64 - 1 are refused before launch; nothing changes
+    before = [lt.hash() for lt in lats]
+    runner.set_counter_base((1 << 64) - 4)
+    with pytest.raises(b.LatError) as e:
+        runner.run(lats, [1, 1, 1, 1])
+    assert e.value.code == b.LAT_EINVAL
+    assert [lt.hash() for lt in lats] == before and [lt.sweep_index for lt in lats] == [12, 10, 9, 11]
+    with pytest.raises(b.LatError):
+        runner.set_counter_base((1 << 64) - 1)
+    runner.set_counter_base(0)
+    obs = runner.run(lats, [2, 2, 2, 2])
+    ref_obs = [r.sweep(2) for r in refs]
     _check_same(lats, refs, obs, ref_obs)
     runner.close()
