@@ -16,12 +16,16 @@
 // code cannot pass the array's name to a kernel (on the host it is only a
 // stand-in symbol); its device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on that device.  Every call reuses the same array: the
+// first call made on that device, and kept for the life of the process (a
+// cudaDeviceReset, which ends the context the address belongs to, is not
+// followed: call no entry point of this file after one).  Every call reuses
+// the same array: the
 // accumulators are cleared on the caller's stream before each use, and two
 // calls whose work overlaps on the GPU (different streams, no ordering
 // between them) race on it.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/lat.h"
@@ -64,6 +68,10 @@ extern "C" int lat_correlation_static(int32_t model, uint32_t L, const void* dev
     if (model != LAT_ISING && model != LAT_BLUME_CAPEL) return LAT_EINVAL;
     if (L < 64 || L % 64 != 0 || L > LAT_MAX_L || (model == LAT_BLUME_CAPEL && L > LAT_MAX_L / 2)) return LAT_EINVAL;
     if (!dev_spins || !cx || !cy || rmax > L / 2 || rmax > LAT_STATIC_RMAX) return LAT_EINVAL;
+    // The correlation kernels read rows as 8-byte (Ising) or 16-byte
+    // (Blume-Capel) words: refuse a pointer that would make those loads
+    // misaligned, before anything is launched.
+    if (reinterpret_cast<uintptr_t>(dev_spins) % 16 != 0) return LAT_EINVAL;
     int err = LAT_OK;
     long long* scratch = static_scratch(&err);
     if (!scratch) return err;

@@ -128,3 +128,27 @@ def test_lut_mode_is_ising_only():
     assert b.lat_footprint(b.make_params(1, 128, 1.0, 1, rng=b.LAT_RNG_TABLE)) == 0
     assert b.lat_footprint(b.make_params(0, 128, 1.0, 1, rng=2)) == 0
     assert b.lat_footprint(b.make_params(0, 128, 1.0, 1, rng=b.LAT_RNG_TABLE)) > 0
+
+
+def test_static_correlation_checks_arguments_before_any_device_call():
+    """lat_correlation_static (the entry point that allocates nothing)
+    rejects a lattice pointer the correlation kernels could not load from
+    (not 16-byte aligned), an rmax beyond its fixed scratch, and bad sizes,
+    with LAT_EINVAL before it touches the device; its limit in lat.h is
+    4096 distances."""
+    text = open(os.path.join(ROOT, "include", "lat.h")).read()
+    m = re.search(r"#define\s+LAT_STATIC_RMAX\s+(\d+)u?", text)
+    assert m and int(m.group(1)) == 4096
+    f = b.load().lat_correlation_static
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    cx = np.zeros(4098, dtype=np.int64)
+    cy = np.zeros(4098, dtype=np.int64)
+    px, py = cx.ctypes.data_as(ctypes.c_void_p), cy.ctypes.data_as(ctypes.c_void_p)
+    fake = 1 << 40   # never dereferenced: every case below must fail its argument checks first
+    for model, L, ptr, rmax in [(0, 256, fake + 8, 4), (1, 256, fake + 4, 4), (0, 256, fake + 1, 0),
+                                (0, 16384, fake, 4097), (0, 256, fake, 129), (0, 100, fake, 4), (2, 256, fake, 4),
+                                (0, 256, None, 4)]:
+        assert f(model, L, ptr, rmax, px, py, None) == b.LAT_EINVAL, (model, L, ptr, rmax)
+    assert f(0, 256, fake, 4, None, py, None) == b.LAT_EINVAL

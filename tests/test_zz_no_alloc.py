@@ -5,8 +5,11 @@ library inside another framework whose caching allocator owns the GPU, or a
 serving loop where cudaMalloc would synchronise the device); its scratch is a
 fixed device array inside the library.  These tests call it through the C
 ABI and check that it returns exactly what lat_correlation returns for the
-same lattice, on consecutive calls that reuse the shared scratch.  The file
-is named so that pytest collects it last.
+same lattice, on consecutive calls that reuse the shared scratch (with
+distances that take both of its kernel paths, the near-distance kernel for
+rmax <= 32 and the window kernels beyond, and rmax = 0), and exactly what
+the CPU oracle computes from the lattice's spins.  The file is named so that
+pytest collects it last.
 """
 import ctypes
 
@@ -39,7 +42,8 @@ def _static_corr(lat, rmax):
 @pytest.mark.parametrize("model,L,T,Delta", [(0, 1024, b.TC_ISING, 0.0), (1, 512, 1.398, 1.0)])
 def test_static_correlation_matches_handle_path_on_consecutive_calls(gpu, model, L, T, Delta):
     lat = b.Lattice(model, L, T, 2024 + model, Delta=Delta)
-    for nsweeps, rmax in [(3, L // 2), (5, 37)]:   # the second call reuses scratch that held longer results
+    # each call reuses scratch that held a longer result before it
+    for nsweeps, rmax in [(3, L // 2), (5, 37), (1, 32), (2, 1), (1, 0), (2, 33)]:
         lat.sweep(nsweeps, record=False)
         ref_x, ref_y = lat.correlation(rmax)
         rc, cx, cy = _static_corr(lat, rmax)
@@ -70,3 +74,17 @@ def test_static_correlation_rejects_sizes_beyond_its_scratch(gpu):
     small = b.Lattice(0, 128, b.TC_ISING, 3)
     assert _static_corr(small, 65)[0] == b.LAT_EINVAL   # beyond L/2
     lat.close(); small.close()
+
+
+@pytest.mark.parametrize("model,L,T,Delta", [(0, 256, b.TC_ISING, 0.0), (1, 192, 1.398, 1.0)])
+def test_static_correlation_equals_the_oracle(gpu, orc, model, L, T, Delta):
+    lat = b.Lattice(model, L, T, 4040 + model, Delta=Delta)
+    for nsweeps, rmax in [(6, L // 2), (3, 32), (2, 0), (4, 77)]:
+        lat.sweep(nsweeps, record=False)
+        s = lat.spins()
+        ox, oy = orc.correlation(s, rmax)
+        for _ in range(2):                      # two calls in a row on the same lattice
+            rc, cx, cy = _static_corr(lat, rmax)
+            assert rc == b.LAT_OK
+            assert np.array_equal(cx, ox) and np.array_equal(cy, oy)
+    lat.close()
