@@ -67,6 +67,9 @@ def _bind(lib):
         "or_run_lut": (None, [u32, u64, P, u32, u32, P, P]),
         "or_lut_word": (u32, [u64, P, u64, u32, u32, i32]),
         "or_sweep_strip_lut": (None, [u32, u64, P, u32, u64, u32, P]),
+        "or_init_window": (None, [i32, u32, u64, u64, u64, u32, u32, P]),
+        "or_sweep_window": (None, [i32, u32, u64, P, u32, u64, u64, u32, u32, P]),
+        "or_sweep_window_lut": (None, [u32, u64, P, u32, u64, u64, u32, u32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -277,3 +280,47 @@ def sweep_strip_lut(L: int, seed: int, tbl: np.ndarray, t: int, y0: int, strip: 
     tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
     _load().or_sweep_strip_lut(L, seed, _p(tbl), t, y0, H, _p(strip))
     return strip
+
+
+# ---- light-cone windows (lattices too large to hold as int8) ------------------
+
+def init_window(model: int, L: int, seed: int, y0: int, x0: int, H: int, Wd: int) -> np.ndarray:
+    """Quench of the H x Wd window at (y0, x0), wrapping modulo L."""
+    w = np.zeros((H, Wd), dtype=np.int8)
+    _load().or_init_window(model, L, seed, y0, x0, H, Wd, _p(w))
+    return w
+
+
+def sweep_window(model: int, L: int, seed: int, thr: np.ndarray, t: int, y0: int, x0: int,
+                 win: np.ndarray) -> np.ndarray:
+    """One non-periodic window sweep in place; the exact block shrinks by 2 per side."""
+    thr = np.ascontiguousarray(thr, dtype=np.uint64)
+    H, Wd = win.shape
+    assert win.dtype == np.int8 and win.flags["C_CONTIGUOUS"] and H <= L and Wd <= L
+    _load().or_sweep_window(model, L, seed, _p(thr), t, y0, x0, H, Wd, _p(win))
+    return win
+
+
+def sweep_window_lut(L: int, seed: int, tbl: np.ndarray, t: int, y0: int, x0: int, win: np.ndarray) -> np.ndarray:
+    tbl = np.ascontiguousarray(tbl, dtype=np.uint32)
+    H, Wd = win.shape
+    assert win.dtype == np.int8 and win.flags["C_CONTIGUOUS"] and H <= L and Wd <= L
+    _load().or_sweep_window_lut(L, seed, _p(tbl), t, y0, x0, H, Wd, _p(win))
+    return win
+
+
+def light_cone(model: int, L: int, seed: int, T: float, t: int, y0: int, x0: int, W: int,
+               Delta: float = 0.0, lut: bool = False) -> np.ndarray:
+    """The W x W block at (y0, x0) after t sweeps from the quench, computed on
+    the (W + 4t)^2 window around it (its light cone)."""
+    m = 2 * t
+    win = init_window(model, L, seed, (y0 - m) % L, (x0 - m) % L, W + 2 * m, W + 2 * m)
+    if lut:
+        tbl = lut_table(1.0, T)
+        for k in range(t):
+            sweep_window_lut(L, seed, tbl, k, (y0 - m) % L, (x0 - m) % L, win)
+    else:
+        thr = thresholds(model, 1.0, T, Delta)
+        for k in range(t):
+            sweep_window(model, L, seed, thr, k, (y0 - m) % L, (x0 - m) % L, win)
+    return win[m:m + W, m:m + W].copy()

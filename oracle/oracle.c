@@ -40,6 +40,10 @@
  *   or_sweep_lut       Kaufman's exact finite-torus energy and Onsager's
  *                      energy reproduced by long runs; frequencies of the
  *                      generated bits; +-flip symmetry.
+ *   or_init_window, or_sweep_window, or_sweep_window_lut  the interior
+ *                      after t calls equals the periodic lattice's after t
+ *                      sweeps (or_run / or_run_lut), windows across the seams
+ *                      (tests/test_oracle_window.py).
  *   or_pack            numpy.packbits (tests/test_oracle_measure.py).
  *   or_hash_words/or_hash  every one-bit change of every canonical word and
  *                      every exchange of two unequal words changes the hash;
@@ -267,6 +271,48 @@ void or_sweep_strip(int model, uint32_t L, uint64_t seed, const uint64_t* thr, u
     }
 }
 
+/* The quench of a window: win[i*Wd + j] = the initial spin of the global    */
+/* site ((y0 + i) mod L, (x0 + j) mod L), i < H, j < Wd.                     */
+void or_init_window(int model, uint32_t L, uint64_t seed, uint64_t y0, uint64_t x0, uint32_t H, uint32_t Wd,
+                    int8_t* win)
+{
+    for (uint64_t i = 0; i < H; ++i)
+        for (uint64_t j = 0; j < Wd; ++j) {
+            uint64_t y = (y0 + i) % L, x = (x0 + j) % L;
+            uint32_t w[4];
+            or_draw(seed, y * L + x, OR_INIT_SWEEP, 0, w);
+            if (model == 0)
+                win[i * Wd + j] = (w[0] >> 31) ? 1 : -1;
+            else
+                win[i * Wd + j] = (int8_t)((int)(((uint64_t)w[0] * 3u) >> 32) - 1);
+        }
+}
+
+/* One sweep of a window that is not periodic (a light-cone check for       */
+/* lattices too large to hold as int8).  win holds H x Wd spins, element    */
+/* (i, j) being the global site ((y0 + i) mod L, (x0 + j) mod L); H, Wd <= L. */
+/* Colour 0 is updated where 1 <= i < H-1 and 1 <= j < Wd-1 (every such site */
+/* has its four neighbours in the window), then colour 1 where 2 <= i < H-2  */
+/* and 2 <= j < Wd-2, each site with its global index for the random stream. */
+/* A phase reads only nearest neighbours, so after t calls the block         */
+/* 2t <= i < H-2t, 2t <= j < Wd-2t equals the periodic lattice after the     */
+/* same t sweeps; the band outside it holds values of no meaning.            */
+void or_sweep_window(int model, uint32_t L, uint64_t seed, const uint64_t* thr, uint32_t sweep, uint64_t y0,
+                     uint64_t x0, uint32_t H, uint32_t Wd, int8_t* win)
+{
+    for (uint32_t colour = 0; colour < 2; ++colour) {
+        uint32_t m = colour == 0 ? 1 : 2;
+        for (uint64_t i = m; i + m < H; ++i)
+            for (uint64_t j = m; j + m < Wd; ++j) {
+                uint64_t y = (y0 + i) % L, x = (x0 + j) % L;
+                if (((x + y) & 1u) != colour) continue;
+                int8_t* c = win + i * Wd + j;
+                int h = c[-(int64_t)Wd] + c[Wd] + c[-1] + c[1];
+                *c = or_update_site(model, *c, h, y * L + x, sweep, colour, seed, thr);
+            }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* The paper's lookup-table random bits for the Ising model (section 3.2).   */
 /* A word of random bits, each set independently with probability           */
@@ -375,6 +421,34 @@ void or_sweep_strip_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint3
                 if (flip) row[x] = (int8_t)(-sv);
             }
         }
+    }
+}
+
+/* The lookup-table sweep of a window that is not periodic (as             */
+/* or_sweep_window, with the flip rule and stream of or_sweep_lut).         */
+void or_sweep_window_lut(uint32_t L, uint64_t seed, const uint32_t tbl[16], uint32_t sweep, uint64_t y0,
+                         uint64_t x0, uint32_t H, uint32_t Wd, int8_t* win)
+{
+    for (uint32_t colour = 0; colour < 2; ++colour) {
+        uint32_t m = colour == 0 ? 1 : 2;
+        for (uint64_t i = m; i + m < H; ++i)
+            for (uint64_t j = m; j + m < Wd; ++j) {
+                uint64_t y = (y0 + i) % L, x = (x0 + j) % L;
+                if (((x + y) & 1u) != colour) continue;
+                int8_t* c = win + i * Wd + j;
+                int sv = *c;
+                int agree = (c[-(int64_t)Wd] == sv) + (c[Wd] == sv) + (c[-1] == sv) + (c[1] == sv);
+                uint64_t w = y * (L / 64) + x / 64;
+                int k = (int)((x % 64) / 2);
+                int flip;
+                if (agree == 4)
+                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k) & or_lut_bit(seed, tbl, w, sweep, colour, 1, k);
+                else if (agree == 3)
+                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k);
+                else
+                    flip = 1;
+                if (flip) *c = (int8_t)(-sv);
+            }
     }
 }
 
