@@ -15,7 +15,7 @@ whole job; the lattice is far larger than L2, so no flush is needed.
 N > 1 (torchrun, one process per GPU) runs independent replicas (seed + rank):
 the path has no exchange step, so there is no collective beyond the timing
 barrier and the max-over-ranks reduction.  --impl reference times the CPU
-oracle on the host on a bounded sample of the same workload.
+oracle on the host (every core) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -424,31 +424,71 @@ def kernel_rev() -> str:
 
 
 # ------------------------------------------------------------ oracle (CPU)
-def oracle_strip_rate(wl, budget_s: float, H: int = 32):
-    """Time the unmodified oracle's strip sweep (one thread) on the workload's
-    lattice: a strip of H rows (+2 halo rows each side) of the quench.
-    Returns (flips_per_ns, sweeps_run, sites_per_sweep)."""
-    import oracle
-    oracle.build()
-    L = wl["L"]
-    thr = oracle.thresholds(wl["model"], 1.0, wl["T"], wl["Delta"])
-    strip = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, H + 4)
-    per_call = (H + 1) * L  # colour 0 on H+2 rows, colour 1 on H rows
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _timed_sweeps(fn, budget_s: float, max_calls: int):
+    """Call fn(i) for i = 0, 1, ... until budget_s has passed (at least once,
+    at most max_calls times); returns (calls, seconds)."""
     n, t0 = 0, time.perf_counter()
     while True:
-        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, n, 0, strip)
+        fn(n)
         n += 1
         el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return per_call * n / (el * 1e9), n, per_call, el
+        if el >= budget_s or n >= max_calls:
+            return n, el
 
 
 def cpu_baseline(wl, budget_s: float = 12.0):
-    rate, n, per_call, el = oracle_strip_rate(wl, budget_s)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d sweeps of a 32-row strip (+halo) of the L=%d lattice, one host thread, %.1f s" %
-                      (n, wl["L"], el)}
+    """The unmodified oracle timed on the host, on one thread and on every
+    core (its row-parallel sweep, which equals the sequential one exactly),
+    over three workloads: the parity configuration whole (Ising L = 256,
+    T = Tc, seed 1234, 100 sweeps), Ising L = 4096 for up to 20 sweeps, and
+    the transition-check sweep of this workload (a strip of rows of the full
+    lattice, with its halo).  The line's value is the all-core rate on the
+    strip, the sample closest to the GPU job."""
+    import oracle
+    oracle.build()
+    nth = host_threads()
+    legs = {}
+
+    def leg(name, model, L, T, Delta, seed, sweeps, frac, strip_rows=None):
+        thr = oracle.thresholds(model, 1.0, T, Delta)
+        out = {}
+        for label, threads in (("one_thread", 1), ("all_cores", nth)):
+            if strip_rows:
+                H = strip_rows
+                base = oracle.init_rows(model, L, seed, L - 2, H + 4)
+                strip = base.copy()
+                fn = lambda i: oracle.sweep_strip_par(model, L, seed, thr, i, 0, strip, threads)
+                per_call = (H + 1) * L  # colour 0 on H+2 rows, colour 1 on H rows
+            else:
+                s = oracle.init(model, L, seed)
+                fn = lambda i: oracle.sweep_par(model, s, seed, thr, i, threads)
+                per_call = L * L
+            b = budget_s * frac * (0.75 if threads == 1 else 0.25)
+            n, el = _timed_sweeps(fn, b, sweeps)
+            out[label] = {"flips_per_ns": per_call * n / (el * 1e9), "sweeps": n, "seconds": round(el, 3)}
+        legs[name] = out
+
+    leg("ising L=256 T=Tc seed=1234, 100 sweeps", 0, 256, TC, 0.0, 1234, 100, 0.1)
+    leg("ising L=4096 T=Tc seed=7, 20 sweeps", 0, 4096, TC, 0.0, 7, 20, 0.45)
+    H = 64
+    strip_name = "%s L=%d: one sweep of a %d-row strip (+2 halo rows each side)" % (
+        "ising" if wl["model"] == 0 else "blume-capel", wl["L"], H)
+    leg(strip_name, wl["model"], wl["L"], wl["T"], wl["Delta"], wl["seed"], 1 << 30, 0.45, strip_rows=H)
+    main = legs[strip_name]
+    return {"value": main["all_cores"]["flips_per_ns"], "unit": UNIT, "cores": nth, "kind": "oracle",
+            "single_thread": main["one_thread"]["flips_per_ns"], "nproc": os.cpu_count(),
+            "sample": "%d sweeps of a %d-row strip (+halo) of the L=%d lattice on %d threads (%.1f s); "
+                      "one thread: %d sweeps" % (main["all_cores"]["sweeps"], H, wl["L"], nth,
+                                                 main["all_cores"]["seconds"], main["one_thread"]["sweeps"]),
+            "legs": legs}
 
 
 def served_bench(args):
@@ -513,36 +553,41 @@ def served_bench(args):
 
 
 def reference(args, wl):
+    """The oracle as the reference arm: every step is one sweep of a strip of
+    rows of the workload's lattice (with its halo), on every host core, the
+    strip sized so that warm-up and timed steps end within about a minute."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
+    nth = host_threads()
     L = wl["L"]
     thr = oracle.thresholds(wl["model"], 1.0, wl["T"], wl["Delta"])
-    # size the strip so that warmup + steps end within about two minutes
-    probe = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, 5)
+    probe = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, 64 + 4)
     t0 = time.perf_counter()
-    oracle.sweep_strip(wl["model"], L, wl["seed"], thr, 0, 0, probe)
-    per_site = (time.perf_counter() - t0) / (2 * L)
+    oracle.sweep_strip_par(wl["model"], L, wl["seed"], thr, 0, 0, probe, nth)
+    per_row = (time.perf_counter() - t0) / 65
     steps_total = max(1, args.steps + args.warmup)
-    H = int(max(1, min(64, 120.0 / steps_total / (per_site * L) - 1)))
+    H = int(max(1, min(1024, 60.0 / steps_total / per_row - 1)))
     strip = oracle.init_rows(wl["model"], L, wl["seed"], L - 2, H + 4)
     for t in range(args.warmup):
-        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, t, 0, strip)
+        oracle.sweep_strip_par(wl["model"], L, wl["seed"], thr, t, 0, strip, nth)
     t0 = time.perf_counter()
     for t in range(args.steps):
-        oracle.sweep_strip(wl["model"], L, wl["seed"], thr, args.warmup + t, 0, strip)
+        oracle.sweep_strip_par(wl["model"], L, wl["seed"], thr, args.warmup + t, 0, strip, nth)
     el = time.perf_counter() - t0
     value = (H + 1) * L * args.steps / (el * 1e9)
-    sample = "each step: one sweep of a %d-row strip (+2 halo rows each side) of the L=%d lattice" % (H, L)
+    sample = ("each step: one sweep of a %d-row strip (+2 halo rows each side) of the L=%d lattice, "
+              "on %d host threads" % (H, L, nth))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8",
             "data": "synthetic",
             "config": {"workload": wl["name"].replace("K sweeps", "%d sweeps" % args.steps), "L": L, "T": wl["T"],
                        "Delta": wl["Delta"], "seed": wl["seed"], "sample_rows": H},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)

@@ -44,6 +44,8 @@
  *                      after t calls equals the periodic lattice's after t
  *                      sweeps (or_run / or_run_lut), windows across the seams
  *                      (tests/test_oracle_window.py).
+ *   or_sweep_par, or_sweep_strip_par  equal to or_sweep / or_sweep_strip for
+ *                      every thread count tried (tests/test_oracle_threads.py).
  *   or_pack            numpy.packbits (tests/test_oracle_measure.py).
  *   or_hash_words/or_hash  every one-bit change of every canonical word and
  *                      every exchange of two unequal words changes the hash;
@@ -55,6 +57,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from Salmon, Moraes, Dror and Shaw, "Parallel      */
@@ -310,6 +315,65 @@ void or_sweep_window(int model, uint32_t L, uint64_t seed, const uint64_t* thr, 
                 int h = c[-(int64_t)Wd] + c[Wd] + c[-1] + c[1];
                 *c = or_update_site(model, *c, h, y * L + x, sweep, colour, seed, thr);
             }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-threaded forms, for timing the oracle on every host core.  A colour  */
+/* phase updates sites that share no bond (section 3.1), so its rows can be   */
+/* shared out among threads in any way: each site is updated by the same      */
+/* or_update_site as in the sequential loops, from the same neighbours, and   */
+/* the result equals or_sweep / or_sweep_strip exactly.  Built with OpenMP    */
+/* when the host compiler has it; otherwise these run on one thread.          */
+/* ------------------------------------------------------------------------ */
+int or_threads_available(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void or_phase_rows(int model, uint32_t L, uint64_t seed, const uint64_t* thr, uint32_t sweep,
+                          uint32_t colour, uint64_t y, int8_t* row, const int8_t* up, const int8_t* down)
+{
+    for (uint64_t x = (colour + y) & 1u; x < L; x += 2) {
+        int h = up[x] + down[x] + row[(x + L - 1) % L] + row[(x + 1) % L];
+        row[x] = or_update_site(model, row[x], h, y * L + x, sweep, colour, seed, thr);
+    }
+}
+
+void or_sweep_par(int model, uint32_t L, uint64_t seed, const uint64_t* thr, uint32_t sweep, int8_t* s,
+                  int nthreads)
+{
+    (void)nthreads;
+    for (uint32_t colour = 0; colour < 2; ++colour) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+        for (int64_t y = 0; y < (int64_t)L; ++y)
+            or_phase_rows(model, L, seed, thr, sweep, colour, (uint64_t)y, s + (size_t)y * L,
+                          s + (size_t)((y + L - 1) % L) * L, s + (size_t)((y + 1) % L) * L);
+    }
+}
+
+/* Strip form (as or_sweep_strip: strip rows 2..H+1 become exact). */
+void or_sweep_strip_par(int model, uint32_t L, uint64_t seed, const uint64_t* thr, uint32_t sweep, uint64_t y0,
+                        uint32_t H, int8_t* strip, int nthreads)
+{
+    (void)nthreads;
+    for (uint32_t colour = 0; colour < 2; ++colour) {
+        int64_t r_lo = colour == 0 ? 1 : 2;
+        int64_t r_hi = colour == 0 ? (int64_t)H + 3 : (int64_t)H + 2;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+        for (int64_t r = r_lo; r < r_hi; ++r) {
+            uint64_t y = (y0 + (uint64_t)L * 4 + (uint64_t)r - 2) % L;
+            or_phase_rows(model, L, seed, thr, sweep, colour, y, strip + (size_t)r * L, strip + (size_t)(r - 1) * L,
+                          strip + (size_t)(r + 1) * L);
+        }
     }
 }
 
