@@ -184,8 +184,9 @@ def run_job(lat, K: int, wl, stream, with_corr: bool = True):
     for the protocol workload, t = floor(2^(x/8) + 0.5) with the section 3.3
     protocol.  Returns (sweep_ms_total, n_sweep_launches, total_draws,
     n_corr_points, obs_count, corr_rows, corr_seconds, n_corr_launches).  CUDA events bracket
-    every lat_sweep call on the lattice's stream, so the sweep-kernel time is
-    measured on the stream the kernels run on."""
+    every lat_sweep and every correlation call on the lattice's stream, so the
+    kernel times are measured on the stream the kernels run on (each call
+    returns host data, so its interval is its kernels plus one small copy)."""
     import numpy as np
     import torch
 
@@ -211,7 +212,8 @@ def run_job(lat, K: int, wl, stream, with_corr: bool = True):
         nobs += len(obs)
         done += n
         if done in meas:
-            t0 = time.perf_counter()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
             if R:
                 out = lat.correlation_protocol(done, R)
                 nds = int(np.sum(out["r"] > 2 * R))
@@ -222,7 +224,9 @@ def run_job(lat, K: int, wl, stream, with_corr: bool = True):
                 lat.correlation(wl["rmax"])
                 rows += wl["rmax"] + 1
                 nlaunch_corr += 1 if wl["rmax"] <= 32 else 2
-            corr_s += time.perf_counter() - t0
+            c1.record(stream)
+            c1.synchronize()
+            corr_s += c0.elapsed_time(c1) / 1e3
             npts += 1
     return sweep_ms, 2 * K, draws, npts, nobs, rows, corr_s, nlaunch_corr
 
@@ -277,10 +281,16 @@ def native(args, wl):
     line_e2e = e2e
     batched = None if args.no_batched else batched_leg(b, stream, device, dist, world)
 
+    # measured issue rates of the integer pipes (the roofline denominators)
+    psampler = ClockSampler(gpu_id_for(local)).start()
+    rates = b.lat_probe_rates()
+    rates["clocks"] = psampler.stop()
+
     # roofline of the dominant kernel (the colour-phase sweep kernel)
     launch_s = (sweep_ms / 1e3) / nlaunch
     draws_per_launch = draws / nlaunch
     achieved = OPS_PER_DRAW * draws_per_launch / launch_s / 1e12
+    imad_peak = rates["imad_ops_per_s"] / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if os.path.exists(prof) and not args.L:
@@ -292,18 +302,45 @@ def native(args, wl):
                 traffic = tr.get("bytes_per_launch")
         except Exception:
             traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "T IMAD-ops/s",
-                "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": imad_peak, "unit": "T IMAD-ops/s",
+                "frac": achieved / imad_peak, "traffic": traffic,
                 "kernel": ("k_ising_phase_lut" if wl.get("rng") else "k_ising_phase") if wl["model"] == 0
                           else "k_bc_phase",
                 "launch_ms": launch_s * 1e3, "draws_per_launch": draws_per_launch,
                 "ops_per_draw": OPS_PER_DRAW,
-                "peak_note": "integer multiply pipe: 152 SM x 64 IMAD lanes/clk x 2070 MHz (derived, not measured); "
-                             "achieved counts 40 IMAD-ops per needed Philox block",
+                "peak_note": "integer multiply pipe, measured: mad.wide.u32 microkernel (lat_probe_rates, two "
+                             "IMAD-ops per widening multiply-add) run on this GPU after the timed job; achieved "
+                             "counts 40 IMAD-ops per needed Philox block",
+                "peak_derived": ALU_PEAK_TOPS, "frac_of_derived": achieved / ALU_PEAK_TOPS,
+                "probe": rates,
                 "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
+    if ncorr and not wl.get("protocol"):
+        roofline["corr"] = corr_roofline(wl, ncorr, corr_s, rates)
     wl = dict(wl, corr_launches=corr_launches, corr_share=corr_s / max_secs, thresholds=thresholds)
     return finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, line_e2e, clocks, dist,
                   batched)
+
+
+def corr_roofline(wl, npts: int, corr_s: float, rates: dict) -> dict:
+    """Roofline of C(r <= rmax) from every site (k_corr_x + k_corr_y).
+
+    Algorithmic work per measurement: 2 (rmax + 1) L^2 / 32 pairs of 32-bit
+    words (both axes, every distance; one XOR and one population count per
+    pair by the definition, Ising).  The kernels pair two word pairs per
+    population count (a carry-save step: sum bit and carry of two XOR words
+    and the running sum, two 3-input logic operations), so per pair they need
+    2 LOP3 on the ALU pipe and 1/2 POPC: the bound is the slower of
+    LOP3 rate / 2 and POPC rate / (1/2), with both rates measured."""
+    L, rmax = wl["L"], wl["rmax"]
+    per = (2 if wl["model"] == 0 else 4) * (rmax + 1) * float(L) * L / 32   # Blume-Capel: two planes
+    achieved = per * npts / corr_s / 1e12
+    lop3, popc = rates["lop3_per_s"] / 1e12, rates["popc_per_s"] / 1e12
+    peak = min(lop3 / 2.0, popc / 0.5)
+    return {"bound": "alu", "kernel": "k_corr_x + k_corr_y", "achieved": achieved, "peak": peak,
+            "unit": "T word-pairs/s", "frac": achieved / peak, "frac_of_popc_one_per_pair": achieved / popc,
+            "pairs_per_measurement": per, "measurements": npts, "ms_per_measurement": corr_s * 1e3 / npts,
+            "peak_note": "carry-save pairing: 2 LOP3 + 1/2 POPC per 32-bit word pair; min(LOP3 rate/2, POPC "
+                         "rate x 2) from lat_probe_rates (measured on this GPU)"}
 
 
 def batched_leg(b, stream, device, dist, world):

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "lat_runner_destroy": (i32, [P]),
         "lat_runner_inject_stall": (i32, [P, u32]),
         "lat_runner_set_counter_base": (i32, [P, u64]),
+        "lat_probe_rates": (i32, [P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -278,6 +279,15 @@ def lat_get_thresholds(h, model: int) -> np.ndarray:
 
 def lat_destroy(h) -> None:
     _check(load().lat_destroy(h), "lat_destroy")
+
+
+def lat_probe_rates() -> dict:
+    """Measured IMAD-op, LOP3 and POPC lane-operation rates of the current device (per second)."""
+    r = np.zeros(3, dtype=np.float64)
+    t = np.zeros(3, dtype=np.float64)
+    _check(load().lat_probe_rates(_ptr(r), _ptr(t)), "lat_probe_rates")
+    return {"imad_ops_per_s": float(r[0]), "lop3_per_s": float(r[1]), "popc_per_s": float(r[2]),
+            "seconds": [float(x) for x in t]}
 
 
 # ---- convenience wrapper over torch device memory ---------------------------

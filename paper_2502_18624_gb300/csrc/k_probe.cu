@@ -1,0 +1,192 @@
+// k_probe.cu -- measured issue rates of the integer pipes the hot path is
+// bound by: 32x32->64 multiply-adds (the Philox4x32-10 rounds of the sweep
+// kernels), 3-input logic operations (the carry-save pairs of the
+// correlation kernels) and population counts.  These rates are the
+// denominators of the library's roofline fractions, measured on the device
+// at hand instead of derived from unit counts and a nominal clock.
+//
+// Each microkernel runs only register arithmetic: NCHAIN independent
+// dependency chains per thread (enough to hide each instruction's latency at
+// full occupancy), unrolled, with every result folded into one value that is
+// stored only if it equals a value it cannot take for the given seed.  So no
+// instruction is dead, and no memory traffic or branch sits in the loop.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/lat.h"
+
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kChains = 8;
+constexpr int kUnroll = 16;
+
+__device__ unsigned int g_probe_sink[4];
+
+__device__ __forceinline__ unsigned long long mad_wide(uint32_t a, uint32_t b, unsigned long long c)
+{
+    unsigned long long d;
+    asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm volatile("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t popc32(uint32_t a)
+{
+    uint32_t d;
+    asm volatile("popc.b32 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
+
+// 2 * kUnroll * kChains IMAD-ops per thread and iteration (each widening
+// multiply-add counts as the two 32-bit halves it produces).
+__global__ void __launch_bounds__(kProbeThreads) k_probe_imad(uint32_t iters, uint32_t seed, uint32_t mult)
+{
+    uint32_t a[kChains];
+    unsigned long long p[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        a[i] = seed ^ (threadIdx.x * kChains + i) ^ (blockIdx.x << 16);
+        p[i] = a[i];
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) {
+                p[i] = mad_wide(a[i], mult, p[i]);
+                a[i] = (uint32_t)(p[i] >> 32);
+            }
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) f ^= a[i] ^ (uint32_t)p[i];
+    if (f == 0x9E3779B9u && seed == 0u) g_probe_sink[0] = f;
+}
+
+// 2 * kUnroll * kChains LOP3 per thread and iteration.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_lop3(uint32_t iters, uint32_t seed, uint32_t c)
+{
+    uint32_t a[kChains], b[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        a[i] = seed ^ (threadIdx.x * kChains + i);
+        b[i] = ~a[i] ^ (blockIdx.x * 0x9E3779B9u);
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) {
+                a[i] = lop3<0x96>(a[i], b[i], c);   // three-input XOR
+                b[i] = lop3<0xE8>(b[i], a[i], c);   // majority
+            }
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) f ^= a[i] + b[i];
+    if (f == 0x7F4A7C15u && seed == 0u) g_probe_sink[1] = f;
+}
+
+// kUnroll * kChains POPC per thread and iteration (plus one multiply-add on
+// the FMA pipe and one add each, on pipes four times wider).
+__global__ void __launch_bounds__(kProbeThreads) k_probe_popc(uint32_t iters, uint32_t seed, uint32_t mult)
+{
+    uint32_t v[kChains], s[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        v[i] = seed ^ (threadIdx.x * kChains + i) ^ (blockIdx.x << 12);
+        s[i] = 0;
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) {
+                s[i] += popc32(v[i]);
+                v[i] = v[i] * mult + s[i];
+            }
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) f ^= s[i] + v[i];
+    if (f == 0x6A09E667u && seed == 0u) g_probe_sink[2] = f;
+}
+
+// Time one launch of a probe (after an untimed one) on stream st.
+template <typename K>
+cudaError_t time_probe(K kernel, int grid, uint32_t iters, uint32_t arg, cudaStream_t st, float* ms)
+{
+    kernel<<<grid, kProbeThreads, 0, st>>>(iters / 8 + 1, 12345u, arg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) {
+        kernel<<<grid, kProbeThreads, 0, st>>>(iters, 12345u, arg);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+template <typename K>
+cudaError_t grid_of(K kernel, int sms, int* grid)
+{
+    int bpsm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, kProbeThreads, 0);
+    *grid = sms * (bpsm < 1 ? 1 : bpsm);
+    return e;
+}
+
+}  // namespace
+
+extern "C" int lat_probe_rates(double rates[3], double seconds[3])
+{
+    if (!rates) return LAT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LAT_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAT_ECUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LAT_ECUDA;
+    // iteration counts sized for roughly 20-60 ms per launch on a GB300
+    const uint32_t iters[3] = {6000, 12000, 4000};
+    float ms[3] = {0, 0, 0};
+    int grid[3] = {0, 0, 0};
+    cudaError_t e = grid_of(k_probe_imad, sms, &grid[0]);
+    if (e == cudaSuccess) e = grid_of(k_probe_lop3, sms, &grid[1]);
+    if (e == cudaSuccess) e = grid_of(k_probe_popc, sms, &grid[2]);
+    if (e == cudaSuccess) e = time_probe(k_probe_imad, grid[0], iters[0], 0xD2511F53u, st, &ms[0]);
+    if (e == cudaSuccess) e = time_probe(k_probe_lop3, grid[1], iters[1], 0xCD9E8D57u, st, &ms[1]);
+    if (e == cudaSuccess) e = time_probe(k_probe_popc, grid[2], iters[2], 0x9E3779B9u, st, &ms[2]);
+    const cudaError_t d = cudaStreamDestroy(st);
+    if (e != cudaSuccess || d != cudaSuccess) return LAT_ECUDA;
+    const double per_thread_iter[3] = {2.0 * kUnroll * kChains, 2.0 * kUnroll * kChains, 1.0 * kUnroll * kChains};
+    for (int k = 0; k < 3; ++k) {
+        const double ops = (double)grid[k] * kProbeThreads * (double)iters[k] * per_thread_iter[k];
+        const double s = ms[k] / 1e3;
+        rates[k] = s > 0 ? ops / s : 0.0;
+        if (seconds) seconds[k] = s;
+    }
+    return LAT_OK;
+}
