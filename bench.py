@@ -290,8 +290,10 @@ def native(args, wl):
     launch_s = (sweep_ms / 1e3) / nlaunch
     draws_per_launch = draws / nlaunch
     achieved = OPS_PER_DRAW * draws_per_launch / launch_s / 1e12
-    imad_peak = rates["imad_ops_per_s"] / 1e12
-    traffic = None
+    # peak: the measured rate of full Philox4x32-10 blocks (ten rounds, the
+    # algorithmic unit of the sweep) at 40 IMAD-ops each
+    imad_peak = OPS_PER_DRAW * rates["philox_blocks_per_s"] / 1e12
+    traffic, inst = None, None
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if os.path.exists(prof) and not args.L:
         try:
@@ -300,20 +302,29 @@ def native(args, wl):
                 tr = json.load(f).get({"ising-protocol": "ising-tc"}.get(args.workload, args.workload), {})
             if tr.get("kernel_rev") == kernel_rev():
                 traffic = tr.get("bytes_per_launch")
+                inst = tr.get("warp_inst_per_launch")
         except Exception:
-            traffic = None
+            traffic, inst = None, None
     roofline = {"bound": "alu", "achieved": achieved, "peak": imad_peak, "unit": "T IMAD-ops/s",
                 "frac": achieved / imad_peak, "traffic": traffic,
                 "kernel": ("k_ising_phase_lut" if wl.get("rng") else "k_ising_phase") if wl["model"] == 0
                           else "k_bc_phase",
                 "launch_ms": launch_s * 1e3, "draws_per_launch": draws_per_launch,
                 "ops_per_draw": OPS_PER_DRAW,
-                "peak_note": "integer multiply pipe, measured: mad.wide.u32 microkernel (lat_probe_rates, two "
-                             "IMAD-ops per widening multiply-add) run on this GPU after the timed job; achieved "
-                             "counts 40 IMAD-ops per needed Philox block",
+                "peak_note": "measured on this GPU after the timed job (lat_probe_rates): full Philox4x32-10 "
+                             "blocks per second from a register-only microkernel, x 40 IMAD-ops (10 rounds x 2 "
+                             "widening multiplies x 2 halves); achieved counts 40 IMAD-ops per needed block",
+                "peak_mad_wide": rates["imad_ops_per_s"] / 1e12, "frac_of_mad_wide": achieved * 1e12 /
+                rates["imad_ops_per_s"],
                 "peak_derived": ALU_PEAK_TOPS, "frac_of_derived": achieved / ALU_PEAK_TOPS,
                 "probe": rates,
-                "hbm_frac_of_measured": (L2 / 4.0) / launch_s / 1e9 / measured_hbm_gbs()}
+                "hbm_frac_of_measured": (L2 / (4.0 if wl["model"] == 0 else 2.0)) / launch_s / 1e9 /
+                measured_hbm_gbs()}
+    if inst:
+        # issue slots: 4 schedulers per SM, one warp instruction each per clock
+        issue_peak = SMS * 4 * (rates["clocks"].get("sm_mhz") or SM_MAX_MHZ) * 1e6
+        roofline["issue_frac"] = inst / launch_s / issue_peak
+        roofline["warp_inst_per_launch"] = inst
     if ncorr and not wl.get("protocol"):
         roofline["corr"] = corr_roofline(wl, ncorr, corr_s, rates)
     wl = dict(wl, corr_launches=corr_launches, corr_share=corr_s / max_secs, thresholds=thresholds)

@@ -381,18 +381,21 @@ int lat_correlation_static(int32_t model, uint32_t L, const void* dev_spins, uin
  *
  * Measured issue rates of the integer pipes the hot path is bound by, the
  * denominators of its roofline fractions (the paper has no counterpart).
- * Runs three register-only microkernels on the current device, each for a
- * few tens of milliseconds at full occupancy, and writes lane-operations per
- * second to rates[0..2]:
+ * Runs register-only microkernels on the current device, each for a few tens
+ * of milliseconds at full occupancy, and writes to rates[0..LAT_PROBE_RATES):
  *   rates[0]  IMAD-ops/s: 32x32->64 multiply-adds (mad.wide.u32, the
- *             Philox4x32-10 round multiply), each counted as two IMAD-ops;
+ *             Philox4x32-10 round multiply), each counted as two IMAD-ops
+ *             (the faster of two chain layouts);
  *   rates[1]  LOP3/s: 3-input logic operations (lop3.b32);
- *   rates[2]  POPC/s: population counts (popc.b32).
- * seconds (may be NULL) receives each kernel's CUDA-event time.  The rates
+ *   rates[2]  POPC/s: population counts (popc.b32);
+ *   rates[3]  Philox4x32-10 blocks/s: full ten-round blocks, all four words;
+ *   rates[4]  32-bit multiply-adds (mad.lo.u32) per second.
+ * seconds (may be NULL) receives each rate's CUDA-event time.  The rates
  * hold at the SM clock during the call, which the caller should record.
  * Uses a private stream and synchronises it; allocates nothing.
  * Errors: LAT_EINVAL (NULL rates), LAT_ECUDA. */
-int lat_probe_rates(double rates[3], double seconds[3]);
+#define LAT_PROBE_RATES 5
+int lat_probe_rates(double rates[LAT_PROBE_RATES], double seconds[LAT_PROBE_RATES]);
 
 /* Static description of an error code. */
 const char* lat_strerror(int code);

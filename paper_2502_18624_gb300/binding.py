@@ -282,12 +282,13 @@ def lat_destroy(h) -> None:
 
 
 def lat_probe_rates() -> dict:
-    """Measured IMAD-op, LOP3 and POPC lane-operation rates of the current device (per second)."""
-    r = np.zeros(3, dtype=np.float64)
-    t = np.zeros(3, dtype=np.float64)
+    """Measured integer-pipe rates of the current device (lane-operations per second;
+    Philox in full blocks per second)."""
+    r = np.zeros(5, dtype=np.float64)
+    t = np.zeros(5, dtype=np.float64)
     _check(load().lat_probe_rates(_ptr(r), _ptr(t)), "lat_probe_rates")
     return {"imad_ops_per_s": float(r[0]), "lop3_per_s": float(r[1]), "popc_per_s": float(r[2]),
-            "seconds": [float(x) for x in t]}
+            "philox_blocks_per_s": float(r[3]), "imad32_per_s": float(r[4]), "seconds": [float(x) for x in t]}
 
 
 # ---- convenience wrapper over torch device memory ---------------------------

@@ -35,70 +35,115 @@ struct Planes {
     static constexpr int n = MODEL == 0 ? 1 : 2;
 };
 
-// Load row y as 32-bit words: Ising plane at dst[0..W32); Blume-Capel n
-// plane at dst[0..W32) and g plane at dst[W32..2 W32).
-template <int MODEL>
-__device__ __forceinline__ void load_row32(const void* spins, uint32_t W, uint64_t y, uint32_t* dst, int lane,
-                                           int nlanes)
+// acc + v on the multiply-add pipe.  `one` is a kernel argument equal to 1,
+// so the multiply cannot be folded away and the sum stays an IMAD, off the
+// ALU pipe that the XORs and carry-save logic of the pairs already fill.
+__device__ __forceinline__ int mad_acc(int acc, uint32_t v, uint32_t one)
 {
-    const uint32_t W32 = 2 * W;
-    if constexpr (MODEL == 0) {
-        const uint2* src = static_cast<const uint2*>(spins) + y * W;
-        for (uint32_t j = lane; j < W; j += nlanes) {
-            const uint2 v = src[j];
-            dst[2 * j] = v.x;
-            dst[2 * j + 1] = v.y;
-        }
-    } else {
-        const uint4* src = static_cast<const uint4*>(spins) + y * W;
-        for (uint32_t j = lane; j < W; j += nlanes) {
-            const uint4 v = src[j];  // n lo, n hi, g lo, g hi
-            dst[2 * j] = v.x;
-            dst[2 * j + 1] = v.y;
-            dst[W32 + 2 * j] = v.z;
-            dst[W32 + 2 * j + 1] = v.w;
+    int r;
+    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(one), "r"(acc));
+    return r;
+}
+
+// One carry-save step of the running sum (ones, carries) with two new words:
+// the new sum bit is ones ^ x1 ^ x2 and the carry is their majority, each
+// one 3-input logic operation.
+__device__ __forceinline__ uint32_t csa_sum(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t csa_carry(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Asynchronous 4-byte copy global -> shared (zero-filled when !ok; src must
+// still be a valid address), and the group fences that order them.
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src, bool ok)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Word j0 of the row rotated right by s bits: bits s..31 of word j0
+// followed by bits 0..s-1 of the next word.  The staged row is extended
+// periodically past its end (row[W32 + i] = row[i]), so no wrap is needed.
+__device__ __forceinline__ uint32_t rot_word(const uint32_t* row, uint32_t j0, uint32_t s)
+{
+    return __funnelshift_r(row[j0], row[j0 + 1], s);
+}
+
+// Stage row y as 32-bit words extended periodically to n >= W32 words
+// (asynchronous copies): word j of the staged row is word j mod W32 of the
+// lattice row.  Ising plane at dst[0..n); Blume-Capel n plane at dst[0..n)
+// and g plane at dst[n..2n).
+template <int MODEL>
+__device__ __forceinline__ void stage_row32_ext(const void* spins, uint32_t W32, uint64_t y, uint32_t n,
+                                                uint32_t* dst, int lane, int nlanes)
+{
+    const uint32_t* src = static_cast<const uint32_t*>(spins) + y * W32 * (MODEL == 0 ? 1 : 2);
+    for (uint32_t j = lane; j < n; j += nlanes) {
+        const uint32_t w = j < W32 ? j : j - W32 * (j / W32);
+        if constexpr (MODEL == 0) {
+            cp_async4(dst + j, src + w, true);
+        } else {  // words (n lo, n hi, g lo, g hi) per 64 sites
+            cp_async4(dst + j, src + 4 * (w / 2) + (w & 1), true);
+            cp_async4(dst + n + j, src + 4 * (w / 2) + 2 + (w & 1), true);
         }
     }
 }
 
-// Word j0 (0 <= j0 < W32) of the row rotated right by s bits: bits s..31 of
-// word j0 followed by bits 0..s-1 of the next word (periodic).
-__device__ __forceinline__ uint32_t rot_word(const uint32_t* row, uint32_t W32, uint32_t j0, uint32_t s)
-{
-    const uint32_t j1 = j0 + 1 == W32 ? 0 : j0 + 1;
-    return __funnelshift_r(row[j0], row[j1], s);
-}
-
 template <int MODEL, int NQ>
 __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, uint32_t L, uint32_t rmax,
-                                                           uint32_t rows_per_block, long long* cx)
+                                                           uint32_t rows_per_block, long long* cx, uint32_t ext,
+                                                           uint32_t nbuf, uint32_t one)
 {
-    // One row at a time is staged for the whole block; warp g of the block
-    // owns word offsets q0 = (blockIdx.y * nwarps + g) * NQ .. + NQ - 1.
+    // One row at a time is worked on by the whole block, extended
+    // periodically to `ext` words (enough for the largest offset any warp of
+    // the grid reads), while the next row is copied into the other of two
+    // buffers (nbuf = 2; with nbuf = 1, for rows too long for two buffers, the
+    // next row is copied after the block is done with this one); warp g of
+    // the block owns word offsets
+    // q0 = (blockIdx.y * nwarps + g) * NQ .. + NQ - 1.
     extern __shared__ uint32_t sm[];
-    const uint32_t W = L / 64, W32 = L / 32;
+    const uint32_t W32 = L / 32;
     const int warp = threadIdx.x >> 5, s = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const uint32_t q0 = (blockIdx.y * nwarps + warp) * NQ;
-    uint32_t* row = sm;
+    constexpr int P = Planes<MODEL>::n;
+    const uint32_t m2 = 0u - 2u * one;  // -2, for the Blume-Capel opposite-sign pairs
     int acc[NQ];        // Ising: carries of the carry-save sums; Blume-Capel: the sums themselves
     uint32_t ones[NQ];  // Ising: carry-save sum bits
 #pragma unroll
     for (int k = 0; k < NQ; ++k) acc[k] = 0, ones[k] = 0;
     const uint32_t ybeg = blockIdx.x * rows_per_block;
     const uint32_t yend = min(ybeg + rows_per_block, L);
+    if (ybeg < yend) stage_row32_ext<MODEL>(spins, W32, ybeg, ext, sm, threadIdx.x, blockDim.x);
+    cp_async_commit();
     for (uint32_t y = ybeg; y < yend; ++y) {
-        __syncthreads();
-        load_row32<MODEL>(spins, W, y, row, threadIdx.x, blockDim.x);
+        const uint32_t* row = sm + (nbuf == 2 ? ((y - ybeg) & 1u) * ext * P : 0u);
+        if (nbuf == 2 && y + 1 < yend)   // the next row, into the other buffer
+            stage_row32_ext<MODEL>(spins, W32, y + 1, ext, sm + ((y + 1 - ybeg) & 1u) * ext * P, threadIdx.x,
+                                   blockDim.x);
+        cp_async_commit();
+        cp_async_wait1();   // this row's copies have landed
         __syncthreads();
         uint32_t win[NQ], wing[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            const uint32_t j = (q0 + k) % W32;
-            win[k] = rot_word(row, W32, j, s);
-            if constexpr (MODEL == 1) wing[k] = rot_word(row + W32, W32, j, s);
+            win[k] = rot_word(row, q0 + k, s);
+            if constexpr (MODEL == 1) wing[k] = rot_word(row + ext, q0 + k, s);
         }
-        uint32_t jn = (q0 + NQ) % W32;  // (i + q0 + NQ) mod W32: the word entering the window
+        uint32_t jn = q0 + NQ;  // i + q0 + NQ: the word entering the window (< ext - 1)
         if constexpr (MODEL == 0) {
             // Words i and i+1 (W32 is even) go through one carry-save step per
             // distance: sum bits stay in ones[k], the carries are counted.
@@ -111,20 +156,21 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
                         uint32_t x1[NQ];
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
-                        win[u % NQ] = rot_word(row, W32, jn, s);
-                        jn = jn + 1 == W32 ? 0 : jn + 1;
+                        win[u % NQ] = rot_word(row, jn, s);
+                        ++jn;
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) {
                             const uint32_t x2 = a2 ^ win[(u + 1 + k) % NQ];
-                            const uint32_t t = ones[k] ^ x1[k];
-                            acc[k] += __popc((ones[k] & x1[k]) | (t & x2));
-                            ones[k] = t ^ x2;
+                            acc[k] = mad_acc(acc[k], __popc(csa_carry(ones[k], x1[k], x2)), one);
+                            ones[k] = csa_sum(ones[k], x1[k], x2);
                         }
-                        win[(u + 1) % NQ] = rot_word(row, W32, jn, s);
-                        jn = jn + 1 == W32 ? 0 : jn + 1;
+                        win[(u + 1) % NQ] = rot_word(row, jn, s);
+                        ++jn;
                     }
                 }
             }
+            __syncthreads();  // every warp is done with this buffer before it is refilled
+            if (nbuf == 1 && y + 1 < yend) stage_row32_ext<MODEL>(spins, W32, y + 1, ext, sm, threadIdx.x, blockDim.x);
             continue;
         }
         for (uint32_t ib = 0; ib < W32; ib += NQ) {
@@ -134,19 +180,22 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
                 if (i < W32) {
                     const uint32_t a = row[i];
                     {
-                        const uint32_t ag = row[W32 + i];
+                        const uint32_t ag = row[ext + i];
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) {
                             const uint32_t both = a & win[(u + k) % NQ];
-                            acc[k] += __popc(both) - 2 * __popc(both & (ag ^ wing[(u + k) % NQ]));
+                            acc[k] = mad_acc(acc[k], __popc(both), one);
+                            acc[k] = mad_acc(acc[k], __popc(both & (ag ^ wing[(u + k) % NQ])), m2);
                         }
-                        win[u] = rot_word(row, W32, jn, s);
-                        wing[u] = rot_word(row + W32, W32, jn, s);
+                        win[u] = rot_word(row, jn, s);
+                        wing[u] = rot_word(row + ext, jn, s);
                     }
-                    jn = jn + 1 == W32 ? 0 : jn + 1;
+                    ++jn;
                 }
             }
         }
+        __syncthreads();  // every warp is done with this buffer before it is refilled
+        if (nbuf == 1 && y + 1 < yend) stage_row32_ext<MODEL>(spins, W32, y + 1, ext, sm, threadIdx.x, blockDim.x);
     }
     const long long rows = yend > ybeg ? (long long)(yend - ybeg) : 0;
 #pragma unroll
@@ -170,9 +219,29 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
 template <int NQ>
 struct YRing {
     static constexpr uint32_t step = 2 * NQ;  // rows staged per step
-    static constexpr uint32_t need = kYWarps * NQ + step + 1;
+    // A step reads ring entries [ys, ys + D + step) while the next step's
+    // entries [ys + D + step, ys + D + 2 step) are copied in: the ring must
+    // hold D + 2 step entries so the two never share a slot.
+    static constexpr uint32_t need = kYWarps * NQ + 2 * step;
     static constexpr uint32_t rows = need <= 64 ? 64 : (need <= 128 ? 128 : 256);
 };
+
+// Asynchronous copy of word j of row y into shared memory: Ising to dn;
+// Blume-Capel n plane to dn and g plane to dg.  Zero when !ok (then no
+// address in the lattice is formed).
+template <int MODEL>
+__device__ __forceinline__ void stage_strip_word(const void* spins, uint32_t W32, uint64_t y, uint32_t j, bool ok,
+                                                 uint32_t* dn, uint32_t* dg)
+{
+    const uint32_t* base = static_cast<const uint32_t*>(spins);
+    if constexpr (MODEL == 0) {
+        cp_async4(dn, ok ? base + y * W32 + j : base, ok);
+    } else {
+        const uint32_t* p = base + y * 2 * W32 + 4 * (j / 2) + (j & 1);
+        cp_async4(dn, ok ? p : base, ok);
+        cp_async4(dg, ok ? p + 2 : base, ok);
+    }
+}
 
 template <int MODEL>
 __device__ __forceinline__ void load_strip_word(const void* spins, uint32_t W32, uint64_t y, uint32_t j, bool ok,
@@ -192,7 +261,8 @@ __device__ __forceinline__ void load_strip_word(const void* spins, uint32_t W32,
 
 template <int MODEL, int NQ>
 __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint32_t L, uint32_t rmax,
-                                                        uint32_t rows_per_block, long long* cy)
+                                                        uint32_t rows_per_block, long long* cy, uint32_t chunks,
+                                                        uint32_t strips, uint32_t one)
 {
     extern __shared__ uint32_t sm[];
     constexpr int P = Planes<MODEL>::n;
@@ -200,50 +270,62 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
     constexpr uint32_t D = kYWarps * NQ;     // distances per block
     const uint32_t W32 = L / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t j0 = blockIdx.x * 32;
+    // Block b covers distance chunk b % chunks of strip (b / chunks) % strips
+    // and row segment b / (chunks * strips): the blocks of one strip and
+    // segment are consecutive, so they run together and read their shared
+    // rows through L2 once.
+    const uint32_t bid = blockIdx.x;
+    const uint32_t chunk = bid % chunks, strip = (bid / chunks) % strips, seg = bid / (chunks * strips);
+    const uint32_t j0 = strip * 32;
     const uint32_t tw = min(32u, W32 - j0);
-    const uint32_t y0 = blockIdx.y * rows_per_block;
-    const uint32_t H = min(rows_per_block, L - y0);
-    const uint32_t r0 = blockIdx.z * D;
+    const uint32_t y0 = seg * rows_per_block;
+    const uint32_t H = min(rows_per_block, L - y0);  // even: L and rows_per_block are even
+    const uint32_t r0 = chunk * D;
+    const uint32_t m2 = 0u - 2u * one;
     uint32_t* ring = sm;                // R x 32 words per plane
-    uint32_t* arow = sm + R * 32 * P;   // 2 NQ x 32 words per plane
+    uint32_t* arow = sm + R * 32 * P;   // two buffers of 2 NQ x 32 words per plane
 
     // Lattice row of ring entry t is (y0 + r0 + t) mod L (staging only, so a
     // plain modulo is cheap next to the pair work).
     const uint32_t rb = (uint32_t)(((uint64_t)y0 + r0) % L);
     auto brow = [L, rb](uint32_t t) { return (uint32_t)(((uint64_t)rb + t) % L); };
-    for (uint32_t t = threadIdx.x; t < D * 32; t += blockDim.x) {  // prefill ring entries 0 .. D-1
-        const uint32_t rr = t / 32, c = t % 32;
-        uint32_t vn, vg;
-        load_strip_word<MODEL>(spins, W32, brow(rr), j0 + c, c < tw, vn, vg);
-        ring[(rr % R) * 32 + c] = vn;
-        if constexpr (P == 2) ring[R * 32 + (rr % R) * 32 + c] = vg;
-    }
-
     constexpr uint32_t S = YRing<NQ>::step;
+    // Copies for the step at ys: A rows ys .. ys+S-1 into buffer b, ring
+    // entries D+ys .. D+ys+S-1.
+    auto stage_step = [&](uint32_t ys, uint32_t b) {
+        uint32_t* ab = arow + b * S * 32 * P;
+        for (uint32_t t = threadIdx.x; t < 2 * S * 32; t += blockDim.x) {
+            const uint32_t rr = (t / 32) % S, c = t % 32;
+            if (t < S * 32) {
+                const uint32_t ya = (uint32_t)(((uint64_t)y0 + ys + rr) % L);
+                stage_strip_word<MODEL>(spins, W32, ya, j0 + c, c < tw && ys + rr < H, ab + rr * 32 + c,
+                                        ab + S * 32 + rr * 32 + c);
+            } else {
+                const uint32_t tb = D + ys + rr;
+                stage_strip_word<MODEL>(spins, W32, brow(tb), j0 + c, c < tw, ring + (tb % R) * 32 + c,
+                                        ring + R * 32 + (tb % R) * 32 + c);
+            }
+        }
+    };
+    for (uint32_t t = threadIdx.x; t < D * 32; t += blockDim.x) {  // ring entries 0 .. D-1
+        const uint32_t rr = t / 32, c = t % 32;
+        stage_strip_word<MODEL>(spins, W32, brow(rr), j0 + c, c < tw, ring + (rr % R) * 32 + c,
+                                ring + R * 32 + (rr % R) * 32 + c);
+    }
+    stage_step(0, 0);
+    cp_async_commit();
+
     const uint32_t g0 = (uint32_t)warp * NQ;
     int acc[NQ];        // Ising: carries of the carry-save sums; Blume-Capel: the sums themselves
     uint32_t ones[NQ];  // Ising: carry-save sum bits
     uint32_t win[NQ], wing[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) acc[k] = 0, ones[k] = 0;
-    for (uint32_t ys = 0; ys < H; ys += S) {
-        __syncthreads();  // the previous step's ring rows and A rows are no longer read
-        for (uint32_t t = threadIdx.x; t < 2 * S * 32; t += blockDim.x) {
-            const uint32_t rr = (t / 32) % S, c = t % 32;
-            uint32_t vn, vg;
-            if (t < S * 32) {
-                const uint32_t ya = (uint32_t)(((uint64_t)y0 + ys + rr) % L);
-                load_strip_word<MODEL>(spins, W32, ya, j0 + c, c < tw && ys + rr < H, vn, vg);
-                arow[rr * 32 + c] = vn;
-                if constexpr (P == 2) arow[S * 32 + rr * 32 + c] = vg;
-            } else {
-                const uint32_t tb = D + ys + rr;
-                load_strip_word<MODEL>(spins, W32, brow(tb), j0 + c, c < tw, vn, vg);
-                ring[(tb % R) * 32 + c] = vn;
-                if constexpr (P == 2) ring[R * 32 + (tb % R) * 32 + c] = vg;
-            }
-        }
+    for (uint32_t ys = 0, it = 0; ys < H; ys += S, ++it) {
+        const uint32_t* ab = arow + (it & 1u) * S * 32 * P;
+        if (ys + S < H) stage_step(ys + S, (it & 1u) ^ 1u);  // the next step, while this one runs
+        cp_async_commit();
+        cp_async_wait1();  // this step's copies have landed
         __syncthreads();
         // window slot k holds ring entry ys + g0 + k at the start of the step
 #pragma unroll
@@ -255,9 +337,8 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
         if constexpr (MODEL == 0) {
 #pragma unroll
             for (int u = 0; u < (int)S; u += 2) {
-                if (ys + u < H) {
-                    const bool second = ys + u + 1 < H;
-                    const uint32_t a1 = arow[u * 32 + lane], a2 = arow[(u + 1) * 32 + lane];
+                if (ys + u < H) {  // then ys + u + 1 < H too (H is even)
+                    const uint32_t a1 = ab[u * 32 + lane], a2 = ab[(u + 1) * 32 + lane];
                     uint32_t x1[NQ];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
@@ -265,10 +346,9 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
                     win[u % NQ] = ring[(tb % R) * 32 + lane];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
-                        const uint32_t x2 = second ? a2 ^ win[(u + 1 + k) % NQ] : 0u;
-                        const uint32_t t = ones[k] ^ x1[k];
-                        acc[k] += __popc((ones[k] & x1[k]) | (t & x2));
-                        ones[k] = t ^ x2;
+                        const uint32_t x2 = a2 ^ win[(u + 1 + k) % NQ];
+                        acc[k] = mad_acc(acc[k], __popc(csa_carry(ones[k], x1[k], x2)), one);
+                        ones[k] = csa_sum(ones[k], x1[k], x2);
                     }
                     tb += 1;
                     win[(u + 1) % NQ] = ring[(tb % R) * 32 + lane];
@@ -278,12 +358,13 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
 #pragma unroll
             for (int u = 0; u < (int)S; ++u) {
                 if (ys + u < H) {
-                    const uint32_t a = arow[u * 32 + lane];
-                    const uint32_t ag = arow[S * 32 + u * 32 + lane];
+                    const uint32_t a = ab[u * 32 + lane];
+                    const uint32_t ag = ab[S * 32 + u * 32 + lane];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
                         const uint32_t both = a & win[(u + k) % NQ];
-                        acc[k] += __popc(both) - 2 * __popc(both & (ag ^ wing[(u + k) % NQ]));
+                        acc[k] = mad_acc(acc[k], __popc(both), one);
+                        acc[k] = mad_acc(acc[k], __popc(both & (ag ^ wing[(u + k) % NQ])), m2);
                     }
                     const uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
                     win[u % NQ] = ring[(tb % R) * 32 + lane];
@@ -291,6 +372,7 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
                 }
             }
         }
+        __syncthreads();  // every warp is done with this A buffer before it is refilled
     }
     const bool colok = (uint32_t)lane < tw;
 #pragma unroll
@@ -323,7 +405,7 @@ constexpr uint32_t kNearStride = 33;  // 32 strip words + the next word
 // along x (X) or y, over all staged rows; m masks the lanes beyond the strip.
 template <int MODEL, bool X, int RB>
 __device__ __forceinline__ void near_rows(const uint32_t (*Sn)[kNearStride], const uint32_t (*Sg)[kNearStride],
-                                          int lane, uint32_t m, long long* v)
+                                          int lane, uint32_t m, uint32_t one, long long* v)
 {
     int acc[8], acc2[8];          // carries of the carry-save sums (Blume-Capel: two chains)
     uint32_t ones[8], ones2[8];   // sum bits
@@ -357,16 +439,16 @@ __device__ __forceinline__ void near_rows(const uint32_t (*Sn)[kNearStride], con
             }
             if constexpr (MODEL == 0) {
                 const uint32_t x1 = (a[0] ^ b[0]) & m, x2 = (a[1] ^ b[1]) & m;
-                acc[d] += __popc((ones[d] & x1) | ((ones[d] ^ x1) & x2));
-                ones[d] = ones[d] ^ x1 ^ x2;
+                acc[d] = mad_acc(acc[d], __popc(csa_carry(ones[d], x1, x2)), one);
+                ones[d] = csa_sum(ones[d], x1, x2);
             } else {
                 // pairs of non-zero sites, and those of opposite sign
                 const uint32_t b1 = a[0] & b[0] & m, b2 = a[1] & b[1] & m;
                 const uint32_t n1 = b1 & (ag[0] ^ bg[0]), n2 = b2 & (ag[1] ^ bg[1]);
-                acc[d] += __popc((ones[d] & b1) | ((ones[d] ^ b1) & b2));
-                ones[d] = ones[d] ^ b1 ^ b2;
-                acc2[d] += __popc((ones2[d] & n1) | ((ones2[d] ^ n1) & n2));
-                ones2[d] = ones2[d] ^ n1 ^ n2;
+                acc[d] = mad_acc(acc[d], __popc(csa_carry(ones[d], b1, b2)), one);
+                ones[d] = csa_sum(ones[d], b1, b2);
+                acc2[d] = mad_acc(acc2[d], __popc(csa_carry(ones2[d], n1, n2)), one);
+                ones2[d] = csa_sum(ones2[d], n1, n2);
             }
         }
     }
@@ -378,7 +460,7 @@ __device__ __forceinline__ void near_rows(const uint32_t (*Sn)[kNearStride], con
 
 template <int MODEL>
 __global__ void __launch_bounds__(256, MODEL == 0 ? 6 : 4) k_corr_near(const void* spins, uint32_t L, uint32_t rmax, long long* cx,
-                                                   long long* cy)
+                                                   long long* cy, uint32_t one)
 {
     constexpr int P = Planes<MODEL>::n;
     constexpr uint32_t NR = kNearRows + kNear;  // staged rows
@@ -404,14 +486,14 @@ __global__ void __launch_bounds__(256, MODEL == 0 ? 6 : 4) k_corr_near(const voi
     const uint32_t (*Sg)[kNearStride] = S[P - 1];
     long long v[8];
     switch (warp) {
-        case 0: near_rows<MODEL, true, 1>(Sn, Sg, lane, m, v); break;
-        case 1: near_rows<MODEL, true, 9>(Sn, Sg, lane, m, v); break;
-        case 2: near_rows<MODEL, true, 17>(Sn, Sg, lane, m, v); break;
-        case 3: near_rows<MODEL, true, 25>(Sn, Sg, lane, m, v); break;
-        case 4: near_rows<MODEL, false, 1>(Sn, Sg, lane, m, v); break;
-        case 5: near_rows<MODEL, false, 9>(Sn, Sg, lane, m, v); break;
-        case 6: near_rows<MODEL, false, 17>(Sn, Sg, lane, m, v); break;
-        default: near_rows<MODEL, false, 25>(Sn, Sg, lane, m, v); break;
+        case 0: near_rows<MODEL, true, 1>(Sn, Sg, lane, m, one, v); break;
+        case 1: near_rows<MODEL, true, 9>(Sn, Sg, lane, m, one, v); break;
+        case 2: near_rows<MODEL, true, 17>(Sn, Sg, lane, m, one, v); break;
+        case 3: near_rows<MODEL, true, 25>(Sn, Sg, lane, m, one, v); break;
+        case 4: near_rows<MODEL, false, 1>(Sn, Sg, lane, m, one, v); break;
+        case 5: near_rows<MODEL, false, 9>(Sn, Sg, lane, m, one, v); break;
+        case 6: near_rows<MODEL, false, 17>(Sn, Sg, lane, m, one, v); break;
+        default: near_rows<MODEL, false, 25>(Sn, Sg, lane, m, one, v); break;
     }
     const bool xw = warp < 4;
     const uint32_t rbase = 8u * (uint32_t)(warp & 3) + 1;
@@ -465,12 +547,23 @@ template <int MODEL, int NQ>
 cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t smem = (size_t)W32 * Planes<MODEL>::n * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_corr_x<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const uint32_t groups = (rmax / 32 + 1 + NQ - 1) / NQ;   // word-offset groups of NQ
     const uint32_t nwarps = groups < (uint32_t)kXWarpsMax ? groups : (uint32_t)kXWarpsMax;
     const uint32_t gy = (groups + nwarps - 1) / nwarps;
+    // the largest word a warp reads is q0 + NQ + W32 (entering words run
+    // from q0 + NQ for W32 steps, plus the next word of each funnel shift),
+    // with q0 < gy * nwarps * NQ
+    const uint32_t ext = gy * nwarps * NQ + NQ + W32 + 1;
+    const size_t one_buf = (size_t)ext * Planes<MODEL>::n * sizeof(uint32_t);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const uint32_t nbuf = 2 * one_buf <= (size_t)optin ? 2u : 1u;  // two row buffers when they fit
+    const size_t smem = nbuf * one_buf;
+    if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(k_corr_x<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     // rows per block: enough blocks for about eight full waves, so the last
     // partial wave costs little; at least 8 rows per block
     int resident = 0;
@@ -483,7 +576,7 @@ cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx
     const uint32_t rmax_rows = (1u << 30) / L;
     rpb = rpb > rmax_rows ? rmax_rows : rpb;
     const dim3 grid((L + rpb - 1) / rpb, gy);
-    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, rpb, cx);
+    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, rpb, cx, ext, nbuf, 1u);
     return cudaGetLastError();
 }
 
@@ -491,7 +584,7 @@ template <int MODEL, int NQ>
 cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t smem = (size_t)(YRing<NQ>::rows + YRing<NQ>::step) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
+    const size_t smem = (size_t)(YRing<NQ>::rows + 2 * YRing<NQ>::step) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_corr_y<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint32_t per_block = kYWarps * NQ;
@@ -505,9 +598,10 @@ cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy
     const uint32_t step = YRing<NQ>::step;
     const uint32_t minrows = 2 * step;
     rpb = rpb < minrows ? minrows : rpb;
-    rpb = (rpb + step - 1) / step * step;
-    const dim3 grid(strips, (L + rpb - 1) / rpb, chunks);
-    k_corr_y<MODEL, NQ><<<grid, kYWarps * 32, smem, st>>>(spins, L, rmax, rpb, cy);
+    rpb = (rpb + step - 1) / step * step;  // a multiple of the (even) step, so every segment has an even row count
+    const uint64_t nblocks = (uint64_t)strips * chunks * ((L + rpb - 1) / rpb);
+    if (nblocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+    k_corr_y<MODEL, NQ><<<(unsigned)nblocks, kYWarps * 32, smem, st>>>(spins, L, rmax, rpb, cy, chunks, strips, 1u);
     return cudaGetLastError();
 }
 
@@ -546,8 +640,8 @@ cudaError_t launch_correlation(int model, const void* spins, uint32_t L, uint32_
     if (e != cudaSuccess) return e;
     if (rmax <= kNear) {
         const dim3 grid((L / 32 + 31) / 32, L / kNearRows);
-        if (model == 0) k_corr_near<0><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy);
-        else k_corr_near<1><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy);
+        if (model == 0) k_corr_near<0><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy, 1u);
+        else k_corr_near<1><<<grid, 256, 0, st>>>(spins, L, rmax, cx, cy, 1u);
         return cudaGetLastError();
     }
     return model == 0 ? launch_xy<0>(spins, L, rmax, cx, cy, st) : launch_xy<1>(spins, L, rmax, cx, cy, st);

@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "../../include/lat.h"
+#include "philox.cuh"
 
 namespace {
 
@@ -71,6 +72,87 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_imad(uint32_t iters, ui
 #pragma unroll
     for (int i = 0; i < kChains; ++i) f ^= a[i] ^ (uint32_t)p[i];
     if (f == 0x9E3779B9u && seed == 0u) g_probe_sink[0] = f;
+}
+
+// The same widening multiply-add with an addend that no instruction writes
+// (one 64-bit constant per chain), so a chain's only dependency is the
+// 32-bit high half it feeds back.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_imad2(uint32_t iters, uint32_t seed, uint32_t mult)
+{
+    uint32_t a[kChains];
+    unsigned long long c[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        a[i] = seed ^ (threadIdx.x * kChains + i) ^ (blockIdx.x << 16);
+        c[i] = ((unsigned long long)(seed + i) << 32) | (threadIdx.x + 7u * i);
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) a[i] = (uint32_t)(mad_wide(a[i], mult, c[i]) >> 32);
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) f ^= a[i];
+    if (f == 0x9E3779B9u && seed == 0u) g_probe_sink[0] = f;
+}
+
+// kUnroll * kChains 32-bit IMAD (mad.lo.u32) per thread and iteration.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_imad32(uint32_t iters, uint32_t seed, uint32_t mult)
+{
+    uint32_t a[kChains], c[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        a[i] = seed ^ (threadIdx.x * kChains + i) ^ (blockIdx.x << 16);
+        c[i] = seed + 0x1000193u * i;
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) {
+                uint32_t d;
+                asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a[i]), "r"(mult), "r"(c[i]));
+                a[i] = d;
+            }
+        }
+    }
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) f ^= a[i];
+    if (f == 0x85EBCA6Bu && seed == 0u) g_probe_sink[3] = f;
+}
+
+// Full Philox4x32-10 blocks (ten rounds, all four output words), kUnroll *
+// 2 per thread and iteration in two independent chains of counters.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_philox(uint32_t iters, uint32_t seed, uint32_t sweep)
+{
+    latk::RoundKeys rk;  // key schedule of Salmon et al.: the Weyl increments per round
+    {
+        uint32_t k0 = 0x89ABCDEFu ^ seed, k1 = 0x01234567u;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            rk.k0[r] = k0;
+            rk.k1[r] = k1;
+            k0 += latk::kWeyl0;
+            k1 += latk::kWeyl1;
+        }
+    }
+    uint32_t f0 = 0, f1 = 0;
+    const uint32_t site = (blockIdx.x * kProbeThreads + threadIdx.x) * 2u;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t ctr = it * kUnroll + u;
+            const uint4 r0 = latk::philox4(site, ctr, sweep, f0 & 1u, rk);
+            const uint4 r1 = latk::philox4(site + 1u, ctr, sweep, f1 & 1u, rk);
+            f0 ^= r0.x ^ r0.y ^ r0.z ^ r0.w;
+            f1 ^= r1.x ^ r1.y ^ r1.z ^ r1.w;
+        }
+    }
+    if ((f0 ^ f1) == 0x27D4EB2Fu && seed == 0u) g_probe_sink[3] = f0;
 }
 
 // 2 * kUnroll * kChains LOP3 per thread and iteration.
@@ -161,7 +243,7 @@ cudaError_t grid_of(K kernel, int sms, int* grid)
 
 }  // namespace
 
-extern "C" int lat_probe_rates(double rates[3], double seconds[3])
+extern "C" int lat_probe_rates(double rates[LAT_PROBE_RATES], double seconds[LAT_PROBE_RATES])
 {
     if (!rates) return LAT_EINVAL;
     int dev = 0, sms = 0;
@@ -170,23 +252,45 @@ extern "C" int lat_probe_rates(double rates[3], double seconds[3])
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LAT_ECUDA;
     // iteration counts sized for roughly 20-60 ms per launch on a GB300
-    const uint32_t iters[3] = {6000, 12000, 4000};
-    float ms[3] = {0, 0, 0};
-    int grid[3] = {0, 0, 0};
-    cudaError_t e = grid_of(k_probe_imad, sms, &grid[0]);
-    if (e == cudaSuccess) e = grid_of(k_probe_lop3, sms, &grid[1]);
-    if (e == cudaSuccess) e = grid_of(k_probe_popc, sms, &grid[2]);
-    if (e == cudaSuccess) e = time_probe(k_probe_imad, grid[0], iters[0], 0xD2511F53u, st, &ms[0]);
-    if (e == cudaSuccess) e = time_probe(k_probe_lop3, grid[1], iters[1], 0xCD9E8D57u, st, &ms[1]);
-    if (e == cudaSuccess) e = time_probe(k_probe_popc, grid[2], iters[2], 0x9E3779B9u, st, &ms[2]);
+    enum { kImad, kImad2, kLop3, kPopc, kPhilox, kImad32, kN };
+    const uint32_t iters[kN] = {6000, 6000, 12000, 4000, 1500, 8000};
+    // lane-operations (blocks for Philox) per thread and iteration
+    const double per_thread_iter[kN] = {2.0 * kUnroll * kChains, 2.0 * kUnroll * kChains, 2.0 * kUnroll * kChains,
+                                        1.0 * kUnroll * kChains, 2.0 * kUnroll, 1.0 * kUnroll * kChains};
+    float ms[kN] = {};
+    int grid[kN] = {};
+    cudaError_t e = grid_of(k_probe_imad, sms, &grid[kImad]);
+    if (e == cudaSuccess) e = grid_of(k_probe_imad2, sms, &grid[kImad2]);
+    if (e == cudaSuccess) e = grid_of(k_probe_lop3, sms, &grid[kLop3]);
+    if (e == cudaSuccess) e = grid_of(k_probe_popc, sms, &grid[kPopc]);
+    if (e == cudaSuccess) e = grid_of(k_probe_philox, sms, &grid[kPhilox]);
+    if (e == cudaSuccess) e = grid_of(k_probe_imad32, sms, &grid[kImad32]);
+    if (e == cudaSuccess) e = time_probe(k_probe_imad, grid[kImad], iters[kImad], 0xD2511F53u, st, &ms[kImad]);
+    if (e == cudaSuccess) e = time_probe(k_probe_imad2, grid[kImad2], iters[kImad2], 0xD2511F53u, st, &ms[kImad2]);
+    if (e == cudaSuccess) e = time_probe(k_probe_lop3, grid[kLop3], iters[kLop3], 0xCD9E8D57u, st, &ms[kLop3]);
+    if (e == cudaSuccess) e = time_probe(k_probe_popc, grid[kPopc], iters[kPopc], 0x9E3779B9u, st, &ms[kPopc]);
+    if (e == cudaSuccess) e = time_probe(k_probe_philox, grid[kPhilox], iters[kPhilox], 17u, st, &ms[kPhilox]);
+    if (e == cudaSuccess) e = time_probe(k_probe_imad32, grid[kImad32], iters[kImad32], 0xD2511F53u, st, &ms[kImad32]);
     const cudaError_t d = cudaStreamDestroy(st);
     if (e != cudaSuccess || d != cudaSuccess) return LAT_ECUDA;
-    const double per_thread_iter[3] = {2.0 * kUnroll * kChains, 2.0 * kUnroll * kChains, 1.0 * kUnroll * kChains};
-    for (int k = 0; k < 3; ++k) {
+    double rate[kN];
+    for (int k = 0; k < kN; ++k) {
         const double ops = (double)grid[k] * kProbeThreads * (double)iters[k] * per_thread_iter[k];
-        const double s = ms[k] / 1e3;
-        rates[k] = s > 0 ? ops / s : 0.0;
-        if (seconds) seconds[k] = s;
+        rate[k] = ms[k] > 0 ? ops / (ms[k] / 1e3) : 0.0;
+    }
+    // rates[0]: the faster of the two widening multiply-add chains
+    const bool second = rate[kImad2] > rate[kImad];
+    rates[0] = second ? rate[kImad2] : rate[kImad];
+    rates[1] = rate[kLop3];
+    rates[2] = rate[kPopc];
+    rates[3] = rate[kPhilox];
+    rates[4] = rate[kImad32];
+    if (seconds) {
+        seconds[0] = (second ? ms[kImad2] : ms[kImad]) / 1e3;
+        seconds[1] = ms[kLop3] / 1e3;
+        seconds[2] = ms[kPopc] / 1e3;
+        seconds[3] = ms[kPhilox] / 1e3;
+        seconds[4] = ms[kImad32] / 1e3;
     }
     return LAT_OK;
 }

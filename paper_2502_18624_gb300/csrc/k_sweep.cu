@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __gr
 template <bool OBS>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_bc_phase(const __grid_constant__ BcPhaseArgs a)
 {
-    __shared__ unsigned long long s_thr[kBcTable];
+    __shared__ uint2 s_thr[kBcTable];
     bc_table128(a.thr, s_thr);
     __syncthreads();
     const BcPhase ph{a.spins, a.L, a.W, a.sweep, a.colour};

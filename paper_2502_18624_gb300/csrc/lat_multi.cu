@@ -119,7 +119,7 @@ __device__ __forceinline__ void ising_tile(const MultiDesc& d, const uint32_t* s
 }
 
 template <bool OBS>
-__device__ __forceinline__ void bc_tile(const MultiDesc& d, const unsigned long long* s_thr, uint32_t sweep,
+__device__ __forceinline__ void bc_tile(const MultiDesc& d, const uint2* s_thr, uint32_t sweep,
                                         uint32_t colour, uint64_t i0, uint64_t i1, PhaseAcc& acc)
 {
     const BcPhase ph{static_cast<ulonglong2*>(d.spins), d.L, d.W, sweep, colour};
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kMultiThreads, MINB)
 {
     __shared__ unsigned long long s_g;
     __shared__ int s_stop;
-    __shared__ unsigned long long s_thr[kBcTable];
+    __shared__ uint2 s_thr[kBcTable];
     __shared__ uint32_t s_lut[kLutSlots];
     const unsigned long long total = ctl->total;
     const uint32_t K = ctl->nphases;

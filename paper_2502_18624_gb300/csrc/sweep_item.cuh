@@ -246,6 +246,12 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
 // of a byte, where the word's active sites take them (no later spreading).
 constexpr int kLutSlots = 86;  // spread4(15) + 1
 
+// 1: search the table level by level across a word's 16 uniforms; 0: one
+// uniform at a time.  Both give the same bits.
+#ifndef LAT_LUT_LEVELS
+#define LAT_LUT_LEVELS 0
+#endif
+
 __host__ __device__ __forceinline__ constexpr uint32_t spread4(uint32_t j)
 {
     return (j & 1u) | ((j & 2u) << 1) | ((j & 4u) << 2) | ((j & 8u) << 3);
@@ -291,6 +297,33 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
         const uint64_t ctr = 4ull * w;                                      // 4w+q never carries into the high word
         const PhiloxChunk pc = philox_chunk((uint32_t)(ctr >> 32), a.sweep, a.colour + 2u, rk);
         uint64_t e0 = 0, e1 = 0;
+#if LAT_LUT_LEVELS
+        // Eight uniforms (two Philox blocks, one bit word) at a time, then
+        // the four search levels one at a time across them, so each level
+        // issues eight independent shared loads instead of one chain of four
+        // per uniform.
+        const uint32_t t8 = s_lut[spread4(8)];
+#pragma unroll
+        for (int hw = 0; hw < 2; ++hw) {
+            uint32_t u[8], js[8];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)(2 * hw + q), pc, rk);
+                u[4 * q] = r.x, u[4 * q + 1] = r.y, u[4 * q + 2] = r.z, u[4 * q + 3] = r.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) js[i] = u[i] >= t8 ? spread4(8) : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(4)] ? spread4(4) : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(2)] ? spread4(2) : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(1)] ? spread4(1) : 0u;
+            const uint64_t lo = js[0] | (js[1] << 8) | (js[2] << 16) | (js[3] << 24);
+            const uint64_t hi = js[4] | (js[5] << 8) | (js[6] << 16) | (js[7] << 24);
+            (hw == 0 ? e0 : e1) = lo | (hi << 32);  // uniforms 8 hw .. 8 hw + 7
+        }
+#else
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)q, pc, rk);
@@ -299,6 +332,7 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
             if (q < 2) e0 |= (uint64_t)b4 << (32 * q);  // uniforms 4q .. 4q+3
             else e1 |= (uint64_t)b4 << (32 * (q - 2));
         }
+#endif
         const uint64_t x0 = e0 << it.p, x1 = e1 << it.p;
         const uint64_t acc4 = it.u4[k] & x0, acc8 = it.u8[k] & x0 & x1;
         it.flip[k] |= acc4 | acc8;
@@ -336,23 +370,31 @@ __host__ __device__ __forceinline__ int bc_value(uint32_t code)
 // The kernels' Blume-Capel table, 128 entries indexed by
 //   code | (h+4) << 2 | b << 6
 // (spin code, neighbour sum h = -4..4 as h+4 in 4 bits, proposal bit b).
-// Entry bits 0..32: the acceptance bound of the 54-entry table (2^32 =
-// always); bits 40..41: code of the proposed value; bits 48..55 and 56..63:
-// s'*h and s*h as signed bytes (the site's share of the bond sum B if the
-// move is accepted or rejected).  Unused indices (code 2, h+4 > 8) hold 0.
+// An entry is (bound, xm): the move is accepted iff word 0 <= bound, and an
+// accepted move XORs the site's code with xm = code ^ (code of the proposed
+// value).  From the 54-entry table's t: bound = 2^32 - 1 when t = 2^32
+// (always), t - 1 when 0 < t < 2^32 (u < t iff u <= t - 1); a move that is
+// never accepted (t = 0) and unused indices (code 2, h+4 > 8) get xm = 0, so
+// whatever the comparison gives, the site keeps its code.
 constexpr int kBcTable = 128;
 
-__device__ __forceinline__ void bc_table128(const unsigned long long* thr54, unsigned long long* t)
+// Sites of one half-item per unrolled step of the Blume-Capel site loop.
+#ifndef LAT_BC_UNROLL
+#define LAT_BC_UNROLL 2
+#endif
+constexpr int kBcUnroll = LAT_BC_UNROLL;
+
+__device__ __forceinline__ void bc_table128(const unsigned long long* thr54, uint2* t)
 {
     for (int i = threadIdx.x; i < kBcTable; i += blockDim.x) {
         const uint32_t code = i & 3u, h4 = (i >> 2) & 15u, b = (uint32_t)i >> 6;
-        unsigned long long e = 0;
+        uint2 e = make_uint2(0u, 0u);
         if (code != 2u && h4 <= 8u) {
-            const int sv = bc_value(code), h = (int)h4 - 4;
+            const int sv = bc_value(code);
+            const unsigned long long th = thr54[((sv + 1) * 2 + (int)b) * 9 + (int)h4];
             const uint32_t next = (kBcNext >> (2u * (code * 2u + b))) & 3u;
-            e = thr54[((sv + 1) * 2 + (int)b) * 9 + (int)h4] | ((unsigned long long)next << 40) |
-                ((unsigned long long)(uint8_t)(int8_t)(bc_value(next) * h) << 48) |
-                ((unsigned long long)(uint8_t)(int8_t)(sv * h) << 56);
+            if (th >= kAlways) e = make_uint2(0xFFFFFFFFu, code ^ next);
+            else if (th > 0) e = make_uint2((uint32_t)th - 1u, code ^ next);
         }
         t[i] = e;
     }
@@ -374,12 +416,16 @@ struct BcPhase {
 // built once per item, bit-sliced for all 64 positions: h + 4 = 2 P + Z,
 // with P (Z) the number of +1 (zero) neighbours, so h+4 needs no
 // subtraction.  Two planes share one word (one at the even, one at the odd
-// positions), so three shifts give a site's code and h+4.  The fused bond
-// sum (colour 1) adds s' * h per active site, h the final neighbour sum (its
+// positions), so three shifts give a site's code and h+4.  Per site the
+// loop only compares word 0 with the entry's bound and adds the entry's
+// code mask at the site's position; the new planes are the old ones XOR
+// those masks.  The fused bond sum (colour 1) is then taken bit-sliced over
+// the item: sum over active sites of s' h = sum over new +1 sites of
+// (h+4) - 4 minus the same over new -1 sites, h the final neighbour sum (its
 // four neighbours are colour 0 and already final).
 template <bool OBS, bool CG>
-__device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const unsigned long long* s_tab,
-                                        uint64_t item, int lane, PhaseAcc& acc)
+__device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const uint2* s_tab, uint64_t item,
+                                        int lane, PhaseAcc& acc)
 {
     const uint32_t y = (uint32_t)(item / a.W);
     const uint32_t j = (uint32_t)(item - (uint64_t)y * a.W);
@@ -398,8 +444,10 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
     if (lane == 31 || j + 1 == a.W) right = ld<CG>(row + (j + 1 == a.W ? 0 : j + 1));
 
     const uint32_t p = (y + a.colour) & 1u;
+    constexpr uint64_t E = kEvenBits;
     // Planes in the shifted frame (active sites at even positions).
     uint64_t wcode, wh01, wh23;  // code; h+4 bits 0,1; h+4 bits 2,3 (even/odd positions)
+    uint64_t H0, H1, H2, H3;     // h+4, bit-sliced (bits 0..3)
     {
         const uint64_t nn_ = vn.x >> p, ng_ = vn.y >> p, sn_ = vs.x >> p, sg_ = vs.y >> p;
         const uint64_t wn_ = ((c.x << 1) | (left.x >> 63)) >> p, wg_ = ((c.y << 1) | (left.y >> 63)) >> p;
@@ -411,7 +459,7 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
         const uint64_t s1 = Z1 ^ P0, c1 = Z1 & P0;
         const uint64_t s2 = Z2 ^ P1 ^ c1, c2 = (Z2 & P1) | (Z2 & c1) | (P1 & c1);
         const uint64_t s3 = P2 ^ c2;
-        constexpr uint64_t E = kEvenBits;
+        H0 = Z0, H1 = s1, H2 = s2, H3 = s3;
         wcode = ((c.x >> p) & E) | (((c.y >> p) & E) << 1);
         wh01 = (Z0 & E) | ((s1 & E) << 1);
         wh23 = (s2 & E) | ((s3 & E) << 1);
@@ -420,37 +468,35 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
     const uint64_t base = (uint64_t)y * a.L + (uint64_t)j * 64u;
     const uint32_t site0 = (uint32_t)base + p;  // site of shifted position 0
     const PhiloxChunk pc = philox_chunk((uint32_t)(base >> 32), a.sweep, a.colour, rk);
-    uint64_t acc_m = 0, acc_c = 0;  // accepted sites (even positions); their new codes (2 bits each)
-    int bsum = 0;                   // sum over active sites of s' * h (fused bond sum)
+    uint64_t fm = 0;  // code masks of the accepted moves (2 bits per active site)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int hs = 32 * half;
         const uint32_t x0 = (uint32_t)(wcode >> hs), x1 = (uint32_t)(wh01 >> hs), x2 = (uint32_t)(wh23 >> hs);
-        uint32_t am = 0, ac = 0;
-#pragma unroll 2
+        uint32_t m = 0;
+#pragma unroll kBcUnroll
         for (int k = 0; k < 16; ++k) {
             const uint32_t b = 2u * k;
             const uint2 r = philox_site_w01(site0 + (uint32_t)hs + b, pc, rk);
             const uint32_t idx = ((x0 >> b) & 3u) | (((x1 >> b) & 3u) << 2) | (((x2 >> b) & 3u) << 4) |
                                  ((r.y & 1u) << 6);
-            const unsigned long long e = s_tab[idx];
-            const uint32_t accept = ((uint32_t)(e >> 32) & 1u) | (r.x < (uint32_t)e ? 1u : 0u);
-            am |= accept << b;
-            ac |= (accept ? (uint32_t)(e >> 40) & 3u : 0u) << b;
-            if constexpr (OBS) bsum += accept ? (int)(int8_t)(e >> 48) : (int)(int8_t)(e >> 56);
+            const uint2 e = s_tab[idx];
+            m += (r.x <= e.x ? e.y : 0u) << b;
         }
-        acc_m |= (uint64_t)am << hs;
-        acc_c |= (uint64_t)ac << hs;
+        fm |= (uint64_t)m << hs;
     }
-    constexpr uint64_t E = kEvenBits;
-    const uint64_t m = acc_m << p;
-    const uint64_t nn = (c.x & ~m) | ((acc_c & E) << p), gg = (c.y & ~m) | (((acc_c >> 1) & E) << p);
+    const uint64_t nn = c.x ^ ((fm & E) << p), gg = c.y ^ (((fm >> 1) & E) << p);
     row[j] = make_ulonglong2(nn, gg);
     acc.D += 32;
     if constexpr (OBS) {
-        acc.B += bsum;
         acc.M += __popcll(nn & ~gg) - __popcll(nn & gg);
         acc.Q += __popcll(nn);
+        // bond sum: new +1 and -1 active sites in the shifted frame
+        const uint64_t n1 = (nn >> p) & E, g1 = (gg >> p) & E;
+        const uint64_t up = n1 & ~g1, dn = n1 & g1;
+        const int hu = __popcll(up & H0) + 2 * __popcll(up & H1) + 4 * __popcll(up & H2) + 8 * __popcll(up & H3);
+        const int hd = __popcll(dn & H0) + 2 * __popcll(dn & H1) + 4 * __popcll(dn & H2) + 8 * __popcll(dn & H3);
+        acc.B += (hu - 4 * __popcll(up)) - (hd - 4 * __popcll(dn));
     }
 }
 
