@@ -155,6 +155,20 @@ int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, l
  * Synchronises the stream only when per_sweep is not NULL. */
 int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep);
 
+/* lat_sweep with the Schwinger-Dyson histogram of Eq. (3) after every sweep,
+ * fused into the sweep kernels (section 4: the identity
+ * <exp(-2 beta s_x h_x)> = 1 is the paper's check of equilibrium).
+ * sd_hist is a host array of 9 * nsweeps int64: entry [i*9 + v+4] = number
+ * of sites with s_x * h_x = v, v = -4..4, h_x the sum of the four
+ * neighbours, in the lattice after sweep i of the call (the same values as
+ * lat_sd_hist after that sweep).  Each colour phase counts its own sites:
+ * the colour-1 sites after their update, the colour-0 sites before their
+ * update in the next sweep; one separate pass over the lattice per call
+ * (per 1024 sweeps) counts the colour-0 sites after the last sweep.
+ * per_sweep as in lat_sweep (may be NULL).  LAT_EINVAL if sd_hist is NULL
+ * and nsweeps > 0, and as lat_sweep otherwise.  Synchronises. */
+int lat_sweep_sd(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep, int64_t* sd_hist);
+
 /* Exact (M, B, Q) of the current lattice by a separate reduction kernel
  * (an independent check of the fused per-sweep values).  Synchronises. */
 int lat_measure(lat_t* h, lat_obs* out);

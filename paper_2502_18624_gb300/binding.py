@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True):
         "lat_lut_table": (i32, [PP, P]),
         "lat_create": (i32, [PP, P, sz, P, ctypes.POINTER(P)]),
         "lat_sweep": (i32, [P, u32, P]),
+        "lat_sweep_sd": (i32, [P, u32, P, P]),
         "lat_measure": (i32, [P, P]),
         "lat_correlation": (i32, [P, u32, P, P]),
         "lat_protocol_rc": (u64, [u32, u64]),
@@ -157,6 +158,15 @@ def lat_sweep(h, nsweeps: int, record: bool = True):
     obs = np.zeros(nsweeps, dtype=OBS_DTYPE) if record else None
     _check(load().lat_sweep(h, nsweeps, _ptr(obs) if record and nsweeps else None), "lat_sweep")
     return obs
+
+
+def lat_sweep_sd(h, nsweeps: int, record: bool = True):
+    """nsweeps sweeps with the fused Schwinger-Dyson histogram after each:
+    returns (records or None, int64 array (nsweeps, 9))."""
+    obs = np.zeros(nsweeps, dtype=OBS_DTYPE) if record else None
+    sd = np.zeros((max(nsweeps, 1), 9), dtype=np.int64)
+    _check(load().lat_sweep_sd(h, nsweeps, _ptr(obs) if record and nsweeps else None, _ptr(sd)), "lat_sweep_sd")
+    return obs, sd[:nsweeps]
 
 
 def lat_measure(h) -> tuple[int, int, int, int]:
@@ -312,6 +322,9 @@ class Lattice:
 
     def sweep(self, n: int, record: bool = True):
         return lat_sweep(self.handle, n, record)
+
+    def sweep_sd(self, n: int, record: bool = True):
+        return lat_sweep_sd(self.handle, n, record)
 
     def measure(self):
         return lat_measure(self.handle)

@@ -123,9 +123,12 @@ __global__ void __launch_bounds__(kThreads) k_spin_counts(const void* spins, uin
     }
 }
 
-// Histogram of s_x * h_x (Eq. (3)), bins v = -4..4 at v + 4.
+// Histogram of s_x * h_x (Eq. (3)), bins v = -4..4 at v + 4, added to hist,
+// over the sites of the colours in the bit mask `colours` (1: x+y even,
+// 2: x+y odd, 3: every site).
 template <int MODEL>
-__global__ void __launch_bounds__(kThreads) k_sd_hist(const void* spins, uint32_t L, uint32_t W, long long* hist)
+__global__ void __launch_bounds__(kThreads) k_sd_hist(const void* spins, uint32_t L, uint32_t W, long long* hist,
+                                                     uint32_t colours)
 {
     long long hcount[9];
 #pragma unroll
@@ -134,6 +137,8 @@ __global__ void __launch_bounds__(kThreads) k_sd_hist(const void* spins, uint32_
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t y = (uint32_t)(i / W), j = (uint32_t)(i - (uint64_t)y * W);
+        // sites of colour c in row y sit at the bit positions b with (b + y) % 2 == c
+        const uint64_t cm = colours == 3u ? ~0ull : 0x5555555555555555ull << ((y + (colours == 2u ? 1u : 0u)) & 1u);
         const uint64_t il = (uint64_t)y * W + (j == 0 ? W - 1 : j - 1);
         const uint64_t ir = (uint64_t)y * W + (j + 1 == W ? 0 : j + 1);
         const uint64_t iu = (uint64_t)(y == 0 ? L - 1 : y - 1) * W + j;
@@ -147,17 +152,18 @@ __global__ void __launch_bounds__(kThreads) k_sd_hist(const void* spins, uint32_
             const uint64_t s1 = dn ^ ds, c1 = dn & ds, s2 = dw ^ de, c2 = dw & de;
             const uint64_t d0 = s1 ^ s2, c3 = s1 & s2;
             const uint64_t d1 = c1 ^ c2 ^ c3, d2 = (c1 & c2) | (c1 & c3) | (c2 & c3);
-            hcount[8] += __popcll(~(d0 | d1 | d2));
-            hcount[6] += __popcll(d0 & ~d1 & ~d2);
-            hcount[4] += __popcll(~d0 & d1 & ~d2);
-            hcount[2] += __popcll(d0 & d1 & ~d2);
-            hcount[0] += __popcll(d2);
+            hcount[8] += __popcll(~(d0 | d1 | d2) & cm);
+            hcount[6] += __popcll(d0 & ~d1 & ~d2 & cm);
+            hcount[4] += __popcll(~d0 & d1 & ~d2 & cm);
+            hcount[2] += __popcll(d0 & d1 & ~d2 & cm);
+            hcount[0] += __popcll(d2 & cm);
         } else {
             const ulonglong2* s = static_cast<const ulonglong2*>(spins);
             const ulonglong2 c = s[i], l = s[il], r = s[ir], u = s[iu], d = s[id];
             const uint64_t nw = (c.x << 1) | (l.x >> 63), gw = (c.y << 1) | (l.y >> 63);
             const uint64_t ne = (c.x >> 1) | (r.x << 63), ge = (c.y >> 1) | (r.y << 63);
             for (int bpos = 0; bpos < 64; ++bpos) {
+                if (!((cm >> bpos) & 1)) continue;
                 const int sv = ((c.x >> bpos) & 1) ? (((c.y >> bpos) & 1) ? -1 : 1) : 0;
                 if (sv == 0) {
                     hcount[4] += 1;
@@ -297,15 +303,21 @@ cudaError_t launch_spin_counts(int model, const void* spins, uint32_t L, uint32_
     return cudaGetLastError();
 }
 
+cudaError_t launch_sd_hist_add(int model, const void* spins, uint32_t L, uint32_t W, long long* hist9,
+                               uint32_t colours, int sms, cudaStream_t st)
+{
+    const int grid = grid_for((uint64_t)L * W, sms, 8);
+    if (model == 0) k_sd_hist<0><<<grid, kThreads, 0, st>>>(spins, L, W, hist9, colours);
+    else k_sd_hist<1><<<grid, kThreads, 0, st>>>(spins, L, W, hist9, colours);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sd_hist(int model, const void* spins, uint32_t L, uint32_t W, long long* hist9, int sms,
                            cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(hist9, 0, 9 * sizeof(long long), st);
     if (e != cudaSuccess) return e;
-    const int grid = grid_for((uint64_t)L * W, sms, 8);
-    if (model == 0) k_sd_hist<0><<<grid, kThreads, 0, st>>>(spins, L, W, hist9);
-    else k_sd_hist<1><<<grid, kThreads, 0, st>>>(spins, L, W, hist9);
-    return cudaGetLastError();
+    return launch_sd_hist_add(model, spins, L, W, hist9, 3u, sms, st);
 }
 
 cudaError_t launch_hash(int model, const void* spins, uint32_t L, uint32_t W, unsigned long long* out, int sms,

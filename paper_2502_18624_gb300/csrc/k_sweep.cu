@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kSweepThreads = 256;
 
-template <int CW, bool OBS>
+template <int CW, bool OBS, bool SD = false>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase(const __grid_constant__ IsingPhaseArgs a)
 {
     const IsingPhase ph{a.spins, a.L, a.W, a.sweep, a.colour, a.thr4, a.thr8, a.mode4, a.mode8};
@@ -27,11 +27,12 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase(const __grid_c
     const int lane = threadIdx.x & 31;
     PhaseAcc acc;
     for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems; item += stride)
-        ising_item<CW, OBS, false>(ph, a.rk, item, lane, acc);
+        ising_item<CW, OBS, false, SD>(ph, a.rk, item, lane, acc);
     flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
+    if constexpr (SD) flush_sd(a.sd, acc);
 }
 
-template <int CW, bool OBS>
+template <int CW, bool OBS, bool SD = false>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
 {
     __shared__ uint32_t s_lut[kLutSlots];
@@ -43,11 +44,12 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __gr
     const int lane = threadIdx.x & 31;
     PhaseAcc acc;
     for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems; item += stride)
-        ising_item_lut<CW, OBS, false>(ph, a.rk, s_lut, item, lane, acc);
+        ising_item_lut<CW, OBS, false, SD>(ph, a.rk, s_lut, item, lane, acc);
     flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
+    if constexpr (SD) flush_sd(a.sd, acc);
 }
 
-template <bool OBS>
+template <bool OBS, bool SD = false>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_bc_phase(const __grid_constant__ BcPhaseArgs a)
 {
     __shared__ uint2 s_thr[kBcTable];
@@ -59,8 +61,9 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_bc_phase(const __grid_cons
     const int lane = threadIdx.x & 31;
     PhaseAcc acc;
     for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems; item += stride)
-        bc_item<OBS, false>(ph, a.rk, s_thr, item, lane, acc);
+        bc_item<OBS, false, SD>(ph, a.rk, s_thr, item, lane, acc);
     flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
+    if constexpr (SD) flush_sd(a.sd, acc);
 }
 
 int blocks_for(uint64_t nitems, int sms, int bpsm)
@@ -90,37 +93,49 @@ cudaError_t query_sweep_occupancy(LaunchShape& ls)
     return e;
 }
 
+// The kernel instance for (words per item, fused observables, fused
+// Schwinger-Dyson histogram).
+template <int CW>
+cudaError_t ising_launch(const IsingPhaseArgs& a, int grid, cudaStream_t st)
+{
+    const bool obs = a.obs != nullptr, sd = a.sd != nullptr;
+    if (a.rng == LAT_RNG_TABLE_MODE) {
+        if (sd) {
+            if (obs) k_ising_phase_lut<CW, true, true><<<grid, kSweepThreads, 0, st>>>(a);
+            else k_ising_phase_lut<CW, false, true><<<grid, kSweepThreads, 0, st>>>(a);
+        } else {
+            if (obs) k_ising_phase_lut<CW, true><<<grid, kSweepThreads, 0, st>>>(a);
+            else k_ising_phase_lut<CW, false><<<grid, kSweepThreads, 0, st>>>(a);
+        }
+    } else if (sd) {
+        if (obs) k_ising_phase<CW, true, true><<<grid, kSweepThreads, 0, st>>>(a);
+        else k_ising_phase<CW, false, true><<<grid, kSweepThreads, 0, st>>>(a);
+    } else {
+        if (obs) k_ising_phase<CW, true><<<grid, kSweepThreads, 0, st>>>(a);
+        else k_ising_phase<CW, false><<<grid, kSweepThreads, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ising_phase(const IsingPhaseArgs& a, const LaunchShape& ls, cudaStream_t st)
 {
     const bool even_words = (a.W % 2) == 0;
     const uint64_t nitems = (uint64_t)a.L * (even_words ? a.W / 2 : a.W);
     const int grid = blocks_for(nitems, ls.sms, a.rng == LAT_RNG_TABLE_MODE ? ls.lut_bpsm : ls.ising_bpsm);
-    if (a.rng == LAT_RNG_TABLE_MODE) {
-        if (even_words) {
-            if (a.obs) k_ising_phase_lut<2, true><<<grid, kSweepThreads, 0, st>>>(a);
-            else k_ising_phase_lut<2, false><<<grid, kSweepThreads, 0, st>>>(a);
-        } else {
-            if (a.obs) k_ising_phase_lut<1, true><<<grid, kSweepThreads, 0, st>>>(a);
-            else k_ising_phase_lut<1, false><<<grid, kSweepThreads, 0, st>>>(a);
-        }
-        return cudaGetLastError();
-    }
-    if (even_words) {
-        if (a.obs) k_ising_phase<2, true><<<grid, kSweepThreads, 0, st>>>(a);
-        else k_ising_phase<2, false><<<grid, kSweepThreads, 0, st>>>(a);
-    } else {
-        if (a.obs) k_ising_phase<1, true><<<grid, kSweepThreads, 0, st>>>(a);
-        else k_ising_phase<1, false><<<grid, kSweepThreads, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    return even_words ? ising_launch<2>(a, grid, st) : ising_launch<1>(a, grid, st);
 }
 
 cudaError_t launch_bc_phase(const BcPhaseArgs& a, const LaunchShape& ls, cudaStream_t st)
 {
     const uint64_t nitems = (uint64_t)a.L * a.W;
     const int grid = blocks_for(nitems, ls.sms, ls.bc_bpsm);
-    if (a.obs) k_bc_phase<true><<<grid, kSweepThreads, 0, st>>>(a);
-    else k_bc_phase<false><<<grid, kSweepThreads, 0, st>>>(a);
+    if (a.sd) {
+        if (a.obs) k_bc_phase<true, true><<<grid, kSweepThreads, 0, st>>>(a);
+        else k_bc_phase<false, true><<<grid, kSweepThreads, 0, st>>>(a);
+    } else {
+        if (a.obs) k_bc_phase<true><<<grid, kSweepThreads, 0, st>>>(a);
+        else k_bc_phase<false><<<grid, kSweepThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

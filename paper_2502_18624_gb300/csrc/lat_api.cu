@@ -55,6 +55,8 @@ Layout layout_of(const lat_params* p)
     off = align_up(off + spins_bytes(p));
     l.obs = off;
     off = align_up(off + (size_t)kObsCap * kObsWords * sizeof(long long));
+    l.sd = off;
+    off = align_up(off + (size_t)kObsCap * 9 * sizeof(long long));
     l.corr = off;
     off = align_up(off + 2 * ((size_t)p->L / 2 + 1) * sizeof(long long));
     l.misc = off;
@@ -234,9 +236,15 @@ int lat_create(const lat_params* p, void* dev_buf, size_t bytes, void* stream, l
     return LAT_OK;
 }
 
-int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
+// nsweeps sweeps; per_sweep (or NULL) receives the fused (M, B, Q) records and
+// sd (or NULL) the fused Schwinger-Dyson histogram after every sweep (9 per
+// sweep).  The histogram of the state after sweep t is taken in two parts:
+// its colour-1 sites after their update in the colour-1 phase of sweep t,
+// its colour-0 sites before their update in the colour-0 phase of sweep
+// t+1; after the last sweep of each batch of records a separate pass counts
+// the colour-0 sites.
+static int sweep_impl(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep, int64_t* sd)
 {
-    const NvtxRange range("lat_sweep");
     if (!h) return LAT_EINVAL;
     if (h->next_sweep + nsweeps > kLastSweep) return LAT_EINVAL;
     const uint32_t L = h->p.L, W = h->W;
@@ -267,22 +275,31 @@ int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
             const cudaError_t e = cudaMemsetAsync(h->obs(), 0, (size_t)batch * kObsWords * sizeof(long long), h->stream);
             if (e != cudaSuccess) return LAT_ECUDA;
         }
+        if (sd) {
+            const cudaError_t e = cudaMemsetAsync(h->sd(), 0, (size_t)batch * 9 * sizeof(long long), h->stream);
+            if (e != cudaSuccess) return LAT_ECUDA;
+        }
         for (uint32_t i = 0; i < batch; ++i) {
             const uint32_t t = (uint32_t)(h->next_sweep + done + i);
             long long* rec = per_sweep ? h->obs() + (size_t)i * kObsWords : nullptr;
             for (uint32_t colour = 0; colour < 2; ++colour) {
                 cudaError_t e;
+                // colour 0 counts the previous record's colour-0 sites, colour 1 this one's colour-1 sites
+                long long* sdrec = !sd ? nullptr : colour == 1 ? h->sd() + (size_t)i * 9
+                                                 : (i > 0 ? h->sd() + (size_t)(i - 1) * 9 : nullptr);
                 if (h->p.model == LAT_ISING) {
                     ia.sweep = t;
                     ia.colour = colour;
                     ia.obs = colour == 1 ? rec : nullptr;
                     ia.draws = rec ? rec + kObsDraws : nullptr;
+                    ia.sd = sdrec;
                     e = launch_ising_phase(ia, h->ls, h->stream);
                 } else {
                     ba.sweep = t;
                     ba.colour = colour;
                     ba.obs = colour == 1 ? rec : nullptr;
                     ba.draws = rec ? rec + kObsDraws : nullptr;
+                    ba.sd = sdrec;
                     e = launch_bc_phase(ba, h->ls, h->stream);
                 }
                 if (e != cudaSuccess) return LAT_ECUDA;
@@ -303,10 +320,35 @@ int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
                 o.draws = (uint64_t)h->host_obs[(size_t)i * kObsWords + kObsDraws];
             }
         }
+        if (sd) {
+            // the last record's colour-0 sites (no later colour-0 phase in this batch)
+            cudaError_t e = launch_sd_hist_add(h->p.model, h->spins(), L, W, h->sd() + (size_t)(batch - 1) * 9, 1u,
+                                               h->ls.sms, h->stream);
+            h->host_sd.resize((size_t)batch * 9);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->host_sd.data(), h->sd(), h->host_sd.size() * sizeof(long long),
+                                    cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return LAT_ECUDA;
+            for (size_t k = 0; k < h->host_sd.size(); ++k) sd[(size_t)done * 9 + k] = h->host_sd[k];
+        }
         done += batch;
     }
     h->next_sweep += nsweeps;
     return LAT_OK;
+}
+
+int lat_sweep(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep)
+{
+    const NvtxRange range("lat_sweep");
+    return sweep_impl(h, nsweeps, per_sweep, nullptr);
+}
+
+int lat_sweep_sd(lat_t* h, uint32_t nsweeps, lat_obs* per_sweep, int64_t* sd_hist)
+{
+    const NvtxRange range("lat_sweep_sd");
+    if (!sd_hist && nsweeps > 0) return LAT_EINVAL;
+    return sweep_impl(h, nsweeps, per_sweep, sd_hist);
 }
 
 int lat_measure(lat_t* h, lat_obs* out)

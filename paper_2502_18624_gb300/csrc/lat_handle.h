@@ -11,7 +11,7 @@
 #include "lat_internal.cuh"
 
 struct Layout {
-    size_t spins, obs, corr, misc, stage, ds, rlist, total, stage_bytes;
+    size_t spins, obs, sd, corr, misc, stage, ds, rlist, total, stage_bytes;
 };
 
 struct lat {
@@ -28,9 +28,11 @@ struct lat {
     latk::LaunchShape ls;
     latk::RoundKeys rk;
     std::vector<long long> host_obs;
+    std::vector<long long> host_sd;
 
     void* spins() const { return buf + lay.spins; }
     long long* obs() const { return reinterpret_cast<long long*>(buf + lay.obs); }
+    long long* sd() const { return reinterpret_cast<long long*>(buf + lay.sd); }
     long long* corr() const { return reinterpret_cast<long long*>(buf + lay.corr); }
     long long* misc() const { return reinterpret_cast<long long*>(buf + lay.misc); }
     int8_t* stage() const { return reinterpret_cast<int8_t*>(buf + lay.stage); }

@@ -30,6 +30,10 @@ cudaError_t launch_spin_counts(int model, const void* spins, uint32_t L, uint32_
                                cudaStream_t st);
 cudaError_t launch_sd_hist(int model, const void* spins, uint32_t L, uint32_t W, long long* hist9, int sms,
                            cudaStream_t st);
+// Adds (no clearing) the histogram of the sites of the colours in the mask
+// `colours` (1: colour 0, 2: colour 1, 3: both) to hist9.
+cudaError_t launch_sd_hist_add(int model, const void* spins, uint32_t L, uint32_t W, long long* hist9,
+                               uint32_t colours, int sms, cudaStream_t st);
 cudaError_t launch_hash(int model, const void* spins, uint32_t L, uint32_t W, unsigned long long* out, int sms,
                         cudaStream_t st);
 cudaError_t launch_unpack_rows(int model, const void* spins, uint32_t L, uint32_t W, uint32_t y0,

@@ -36,6 +36,7 @@ struct IsingPhaseArgs {
     uint32_t mode4, mode8;  // ClassMode of the two uphill classes
     long long* obs;         // colour-1 phase: record to accumulate (M, B, Q); else null
     long long* draws;       // counter of Philox draws to accumulate, or null
+    long long* sd;          // 9 counters of the fused Schwinger-Dyson histogram of the active sites, or null
     uint32_t rng;           // LAT_RNG_SITE or LAT_RNG_TABLE
     uint32_t lut[16];       // LAT_RNG_TABLE lookup table
     RoundKeys rk;
@@ -47,6 +48,7 @@ struct BcPhaseArgs {
     uint32_t sweep, colour;
     long long* obs;
     long long* draws;
+    long long* sd;      // as in IsingPhaseArgs
     RoundKeys rk;
     unsigned long long thr[54];  // acceptance table (2^32 = always)
 };

@@ -42,10 +42,25 @@ __device__ __forceinline__ T ld(const T* p)
 }
 
 // Per-thread partial sums of one phase: (M, B, Q) of the fused reduction
-// and the number of Philox draws the phase needed.
+// and the number of Philox draws the phase needed; with the fused
+// Schwinger-Dyson histogram, the counts of the phase's active sites by
+// s_x * h_x (bin v + 4, v = -4..4).  Per thread these stay far below 2^31
+// (a grid-stride thread visits at most a few million sites).
 struct PhaseAcc {
     long long M = 0, B = 0, Q = 0, D = 0;
+    int sd[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+// Add one thread's histogram to the 9 device counters hist (one atomic per
+// bin and warp).
+__device__ __forceinline__ void flush_sd(long long* hist, const PhaseAcc& a)
+{
+#pragma unroll
+    for (int v = 0; v < 9; ++v) {
+        const long long c = warp_sum((long long)a.sd[v]);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(hist + v), (unsigned long long)c);
+    }
+}
 
 __device__ __forceinline__ void flush_acc(long long* obs, long long* draws, PhaseAcc a)
 {
@@ -99,9 +114,10 @@ struct IsingItem {
     uint64_t amask;
     uint64_t c[CW], flip[CW], u8[CW], u4[CW];
     int dpre;  // disagreeing bonds of active sites after the flips decided so far
+    int n2, n3, n4;  // SD: active sites with 2, 3, 4 disagreeing neighbours (they flip whatever is drawn)
 };
 
-template <int CW, bool OBS, bool CG>
+template <int CW, bool OBS, bool CG, bool SD = false>
 __device__ __forceinline__ void ising_classify(const IsingPhase& a, uint64_t item, int lane, bool modes,
                                                IsingItem<CW>& it)
 {
@@ -148,11 +164,18 @@ __device__ __forceinline__ void ising_classify(const IsingPhase& a, uint64_t ite
     const uint64_t amask = kEvenBits << it.p;
     it.amask = amask;
     it.dpre = 0;
+    it.n2 = it.n3 = it.n4 = 0;
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
         const uint64_t dn = c[k] ^ n[k], ds = c[k] ^ s[k], dw = c[k] ^ w[k], de = c[k] ^ e[k];
         const uint64_t x1 = dn ^ ds, a1 = dn & ds;
         const uint64_t x2 = dw ^ de, a2 = dw & de;
+        if constexpr (SD) {
+            // disagreements d = (x1 + 2 a1) + (x2 + 2 a2): d = 4, 3, 2
+            it.n4 += __popcll(a1 & a2 & amask);
+            it.n3 += __popcll(((a1 & x2) | (a2 & x1)) & amask);
+            it.n2 += __popcll(((x1 & x2) | (a1 & ~(x2 | a2)) | (a2 & ~(x1 | a1))) & amask);
+        }
         const uint64_t eq3 = (x1 ^ x2) & ~(a1 | a2);  // exactly one neighbour differs
         const uint64_t eq4 = ~(dn | ds | dw | de);    // none differs
         it.u8[k] = eq4 & amask;
@@ -166,10 +189,38 @@ __device__ __forceinline__ void ising_classify(const IsingPhase& a, uint64_t ite
     }
 }
 
-// Store the new words and add the fused observables.
-template <int CW, bool OBS>
-__device__ __forceinline__ void ising_finish(IsingItem<CW>& it, PhaseAcc& acc)
+// Store the new words and add the fused observables.  SD: the histogram
+// of s h = 4 - 2 d over the item's active sites, d the number of
+// disagreeing neighbours: before the update (post = false: colour 0, whose
+// neighbours are final at the end of the previous sweep) or after it (post:
+// colour 1, whose neighbours are final).  A site with d >= 2 always flips
+// (d -> 4 - d); one with d = 0 or 1 flips as drawn (d -> 4 or 3).
+template <int CW, bool OBS, bool SD = false>
+__device__ __forceinline__ void ising_finish(IsingItem<CW>& it, PhaseAcc& acc, bool post = false)
 {
+    if constexpr (SD) {
+        int f8 = 0, f4 = 0, u8 = 0, u4 = 0;  // flipped / all sites of the two drawn classes
+#pragma unroll
+        for (int k = 0; k < CW; ++k) {
+            u8 += __popcll(it.u8[k]);
+            u4 += __popcll(it.u4[k]);
+            f8 += __popcll(it.u8[k] & it.flip[k]);
+            f4 += __popcll(it.u4[k] & it.flip[k]);
+        }
+        if (post) {
+            acc.sd[8] += it.n4 + u8 - f8;  // d' = 0
+            acc.sd[6] += it.n3 + u4 - f4;  // d' = 1
+            acc.sd[4] += it.n2;            // d' = 2
+            acc.sd[2] += f4;               // d' = 3
+            acc.sd[0] += f8;               // d' = 4
+        } else {
+            acc.sd[8] += u8;
+            acc.sd[6] += u4;
+            acc.sd[4] += it.n2;
+            acc.sd[2] += it.n3;
+            acc.sd[0] += it.n4;
+        }
+    }
     uint64_t cn[CW];
 #pragma unroll
     for (int k = 0; k < CW; ++k) cn[k] = it.c[k] ^ it.flip[k];
@@ -186,12 +237,12 @@ __device__ __forceinline__ void ising_finish(IsingItem<CW>& it, PhaseAcc& acc)
     }
 }
 
-template <int CW, bool OBS, bool CG>
+template <int CW, bool OBS, bool CG, bool SD = false>
 __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys& rk, uint64_t item, int lane,
                                            PhaseAcc& acc)
 {
     IsingItem<CW> it;
-    ising_classify<CW, OBS, CG>(a, item, lane, true, it);
+    ising_classify<CW, OBS, CG, SD>(a, item, lane, true, it);
     const uint64_t drw8 = a.mode8 == kDraw ? ~0ull : 0ull;
     const uint64_t drw4 = a.mode4 == kDraw ? ~0ull : 0ull;
     uint64_t need[CW];
@@ -237,7 +288,7 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
             if constexpr (OBS) it.dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
         }
     }
-    ising_finish<CW, OBS>(it, acc);
+    ising_finish<CW, OBS, SD>(it, acc, a.colour == 1);
 }
 
 // The 16-entry table is searched in "spread" form: entry j sits at slot
@@ -245,12 +296,6 @@ __device__ __forceinline__ void ising_item(const IsingPhase& a, const RoundKeys&
 // binary search yields the four random bits already at the even positions
 // of a byte, where the word's active sites take them (no later spreading).
 constexpr int kLutSlots = 86;  // spread4(15) + 1
-
-// 1: search the table level by level across a word's 16 uniforms; 0: one
-// uniform at a time.  Both give the same bits.
-#ifndef LAT_LUT_LEVELS
-#define LAT_LUT_LEVELS 0
-#endif
 
 __host__ __device__ __forceinline__ constexpr uint32_t spread4(uint32_t j)
 {
@@ -284,12 +329,12 @@ __device__ __forceinline__ uint32_t lut_find_spread(const uint32_t* ts, uint32_t
 // 4i+3, which sit at bits 8i + 2b (+ the row's colour parity).  A 3-agree
 // site flips iff its e0 bit is set, a 4-agree site iff its e0 and e1 bits
 // are.
-template <int CW, bool OBS, bool CG>
+template <int CW, bool OBS, bool CG, bool SD = false>
 __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundKeys& rk, const uint32_t* s_lut,
                                                uint64_t item, int lane, PhaseAcc& acc)
 {
     IsingItem<CW> it;
-    ising_classify<CW, OBS, CG>(a, item, lane, false, it);
+    ising_classify<CW, OBS, CG, SD>(a, item, lane, false, it);
     acc.D += 4 * CW;
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
@@ -297,33 +342,6 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
         const uint64_t ctr = 4ull * w;                                      // 4w+q never carries into the high word
         const PhiloxChunk pc = philox_chunk((uint32_t)(ctr >> 32), a.sweep, a.colour + 2u, rk);
         uint64_t e0 = 0, e1 = 0;
-#if LAT_LUT_LEVELS
-        // Eight uniforms (two Philox blocks, one bit word) at a time, then
-        // the four search levels one at a time across them, so each level
-        // issues eight independent shared loads instead of one chain of four
-        // per uniform.
-        const uint32_t t8 = s_lut[spread4(8)];
-#pragma unroll
-        for (int hw = 0; hw < 2; ++hw) {
-            uint32_t u[8], js[8];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)(2 * hw + q), pc, rk);
-                u[4 * q] = r.x, u[4 * q + 1] = r.y, u[4 * q + 2] = r.z, u[4 * q + 3] = r.w;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) js[i] = u[i] >= t8 ? spread4(8) : 0u;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(4)] ? spread4(4) : 0u;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(2)] ? spread4(2) : 0u;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) js[i] += u[i] >= s_lut[js[i] + spread4(1)] ? spread4(1) : 0u;
-            const uint64_t lo = js[0] | (js[1] << 8) | (js[2] << 16) | (js[3] << 24);
-            const uint64_t hi = js[4] | (js[5] << 8) | (js[6] << 16) | (js[7] << 24);
-            (hw == 0 ? e0 : e1) = lo | (hi << 32);  // uniforms 8 hw .. 8 hw + 7
-        }
-#else
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)q, pc, rk);
@@ -332,13 +350,12 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
             if (q < 2) e0 |= (uint64_t)b4 << (32 * q);  // uniforms 4q .. 4q+3
             else e1 |= (uint64_t)b4 << (32 * (q - 2));
         }
-#endif
         const uint64_t x0 = e0 << it.p, x1 = e1 << it.p;
         const uint64_t acc4 = it.u4[k] & x0, acc8 = it.u8[k] & x0 & x1;
         it.flip[k] |= acc4 | acc8;
         if constexpr (OBS) it.dpre += 2 * __popcll(acc4) + 4 * __popcll(acc8);
     }
-    ising_finish<CW, OBS>(it, acc);
+    ising_finish<CW, OBS, SD>(it, acc, a.colour == 1);
 }
 
 // Three-bit sum of four one-bit words (bit-sliced): returns b0 + 2 b1 + 4 b2.
@@ -423,7 +440,7 @@ struct BcPhase {
 // the item: sum over active sites of s' h = sum over new +1 sites of
 // (h+4) - 4 minus the same over new -1 sites, h the final neighbour sum (its
 // four neighbours are colour 0 and already final).
-template <bool OBS, bool CG>
+template <bool OBS, bool CG, bool SD = false>
 __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, const uint2* s_tab, uint64_t item,
                                         int lane, PhaseAcc& acc)
 {
@@ -497,6 +514,23 @@ __device__ __forceinline__ void bc_item(const BcPhase& a, const RoundKeys& rk, c
         const int hu = __popcll(up & H0) + 2 * __popcll(up & H1) + 4 * __popcll(up & H2) + 8 * __popcll(up & H3);
         const int hd = __popcll(dn & H0) + 2 * __popcll(dn & H1) + 4 * __popcll(dn & H2) + 8 * __popcll(dn & H3);
         acc.B += (hu - 4 * __popcll(up)) - (hd - 4 * __popcll(dn));
+    }
+    if constexpr (SD) {
+        // Histogram of s h over the active sites: before the update in the
+        // colour-0 phase, after it in the colour-1 phase (h is final in both,
+        // the neighbours being of the other colour).  s = 0 (code n clear)
+        // gives bin 4; s = +1 bin h + 4 = H; s = -1 bin 4 - h = 8 - H.
+        const bool post = a.colour == 1;
+        const uint64_t sn = ((post ? nn : c.x) >> p) & E, sg = ((post ? gg : c.y) >> p) & E;
+        const uint64_t up = sn & ~sg, dn = sn & sg;
+        acc.sd[4] += 32 - __popcll(sn);
+#pragma unroll
+        for (int k = 0; k <= 8; ++k) {
+            const uint64_t m = ((k & 1) ? H0 : ~H0) & ((k & 2) ? H1 : ~H1) & ((k & 4) ? H2 : ~H2) &
+                               ((k & 8) ? H3 : ~H3);
+            acc.sd[k] += __popcll(up & m);
+            acc.sd[8 - k] += __popcll(dn & m);
+        }
     }
 }
 
