@@ -180,6 +180,16 @@ int lat_measure(lat_t* h, lat_obs* out);
  * arrays of rmax+1 entries.  rmax must be <= L/2 (LAT_EINVAL).  Synchronises. */
 int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy);
 
+/* lat_correlation without waiting: the correlation kernels and the copies
+ * of the sums into cx and cy are enqueued on the handle's stream and the
+ * call returns.  cx and cy (rmax+1 entries each) hold the sums once the
+ * stream has passed this point (cudaStreamSynchronize, or any later call on
+ * the same stream that synchronises it); they should be page-locked host
+ * memory, without which the copies wait for the stream.  A later
+ * correlation call on the same handle reuses its device accumulators after
+ * this one, in stream order.  Errors as lat_correlation. */
+int lat_correlation_async(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy);
+
 /* The correlation protocol of section 3.3.  Every site is a source for
  * r <= 2R.  Beyond that, only one site per R x R square is a source (its
  * top-left corner, x % R == 0 and y % R == 0), and the distances are:
@@ -253,6 +263,10 @@ int lat_sd_hist(lat_t* h, int64_t* hist);
  * one plane (bit set iff s = +1); Blume-Capel plane 0 (bit set iff s != 0)
  * at words 0..L*W-1 then plane 1 (bit set iff s = -1).  Synchronises. */
 int lat_hash(lat_t* h, uint64_t* out);
+
+/* lat_hash without waiting: the hash is written to *out (page-locked host
+ * memory) once the handle's stream has passed this point. */
+int lat_hash_async(lat_t* h, uint64_t* out);
 
 /* Copy the whole lattice to host int8 values (L*L bytes, row-major,
  * s[y*L + x]).  Synchronises. */
@@ -347,14 +361,33 @@ int lat_runner_set_counter_base(lat_runner_t* r, uint64_t base);
  * max_sweeps, each handle at most once, Ising and Blume-Capel L <= 2^19.
  * per_sweep may be NULL, or an array of n host pointers (each NULL or of
  * nsweeps[i] records) that receive the exact (M, B, Q) and draw count after
- * every sweep, as lat_sweep would.  The call first synchronises every
- * handle's own stream, and synchronises the runner's stream before it
- * returns.  Errors: LAT_EINVAL (including a run whose tile counters would
+ * every sweep, as lat_sweep would.  The run is ordered after all earlier
+ * work of every handle (by stream order when a handle uses the runner's
+ * stream, else by a device-side wait on the handle's stream), and the call
+ * synchronises the runner's stream before it returns.  Errors: LAT_EINVAL (including a run whose tile counters would
  * not fit, see lat_runner_set_counter_base), LAT_ECUDA, LAT_ETIMEDOUT, and LAT_ESTATE if
  * the tile maps built on the host fail their consistency check (an internal
  * error; nothing is launched). */
 int lat_runner_run(lat_runner_t* r, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
                    lat_obs* const* per_sweep);
+
+/* lat_runner_run in two halves, so that the host can prepare other work
+ * while the run is on the device.  lat_runner_submit checks the arguments
+ * (as lat_runner_run), orders the run after the lattices' earlier work as
+ * lat_runner_run does, enqueues it on the runner's stream and returns
+ * without waiting.
+ * lat_runner_collect waits for it, then writes the per-sweep records
+ * (per_sweep as in lat_runner_run; may be NULL) and advances the lattices'
+ * sweep indices.  Between the two, a lattice of the run may only be given
+ * work that is ordered after the run on the runner's stream (for example
+ * lat_correlation_async on a handle created on that stream); no second run
+ * may be submitted (LAT_ESTATE); the runner's other settings may be changed
+ * and apply to later runs.  lat_runner_collect without a pending run is
+ * LAT_ESTATE; a run whose device waits timed out is collected as
+ * LAT_ETIMEDOUT, with its lattices in an unspecified state and their sweep
+ * indices unchanged. */
+int lat_runner_submit(lat_runner_t* r, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps);
+int lat_runner_collect(lat_runner_t* r, lat_obs* const* per_sweep);
 
 /* Release the runner (and its buffer, if the library allocated it). */
 int lat_runner_destroy(lat_runner_t* r);

@@ -97,6 +97,10 @@ def load(build_if_missing: bool = True):
         "lat_runner_destroy": (i32, [P]),
         "lat_runner_inject_stall": (i32, [P, u32]),
         "lat_runner_set_counter_base": (i32, [P, u64]),
+        "lat_runner_submit": (i32, [P, P, u32, P]),
+        "lat_runner_collect": (i32, [P, P]),
+        "lat_correlation_async": (i32, [P, u32, P, P]),
+        "lat_hash_async": (i32, [P, P]),
         "lat_probe_rates": (i32, [P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -427,6 +431,36 @@ def lat_runner_run(r, handles, nsweeps, record: bool = True):
     return outs
 
 
+def lat_runner_submit(r, handles, nsweeps) -> None:
+    """Enqueue a run (advance handles[i] by nsweeps[i]) without waiting."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    ns = np.ascontiguousarray(nsweeps, dtype=np.uint32)
+    _check(load().lat_runner_submit(r, hs, n, _ptr(ns)), "lat_runner_submit")
+
+
+def lat_runner_collect(r, nsweeps, record: bool = True):
+    """Wait for the submitted run; per-sweep record arrays (or None)."""
+    n = len(nsweeps)
+    outs = [np.zeros(int(k), dtype=OBS_DTYPE) for k in nsweeps] if record else None
+    ptrs = (ctypes.c_void_p * n)(*[o.ctypes.data if (o is not None and o.size) else None for o in outs]) \
+        if record else None
+    _check(load().lat_runner_collect(r, ptrs), "lat_runner_collect")
+    return outs
+
+
+def lat_correlation_async(h, rmax: int, cx: np.ndarray, cy: np.ndarray) -> None:
+    """Enqueue C(r <= rmax) into cx, cy (int64, rmax+1 each; page-locked memory for no wait)."""
+    assert cx.dtype == np.int64 and cy.dtype == np.int64 and cx.size > rmax and cy.size > rmax
+    _check(load().lat_correlation_async(h, rmax, _ptr(cx), _ptr(cy)), "lat_correlation_async")
+
+
+def lat_hash_async(h, out: np.ndarray) -> None:
+    """Enqueue the lattice hash into out[0] (uint64, page-locked memory for no wait)."""
+    assert out.dtype == np.uint64 and out.size >= 1
+    _check(load().lat_hash_async(h, _ptr(out)), "lat_hash_async")
+
+
 def lat_runner_inject_stall(r, index: int) -> None:
     _check(load().lat_runner_inject_stall(r, index), "lat_runner_inject_stall")
 
@@ -469,6 +503,12 @@ class Runner:
 
     def run(self, lattices, nsweeps, record: bool = True):
         return lat_runner_run(self.handle, [lt.handle for lt in lattices], nsweeps, record)
+
+    def submit(self, lattices, nsweeps) -> None:
+        lat_runner_submit(self.handle, [lt.handle for lt in lattices], nsweeps)
+
+    def collect(self, nsweeps, record: bool = True):
+        return lat_runner_collect(self.handle, nsweeps, record)
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -383,6 +383,20 @@ int lat_correlation(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy)
     return cuda_err(e);
 }
 
+int lat_correlation_async(lat_t* h, uint32_t rmax, int64_t* cx, int64_t* cy)
+{
+    const NvtxRange range("lat_correlation_async");
+    if (!h || !cx || !cy || rmax > h->p.L / 2) return LAT_EINVAL;
+    long long* dcx = h->corr();
+    long long* dcy = dcx + (rmax + 1);
+    cudaError_t e = launch_correlation(h->p.model, h->spins(), h->p.L, h->W, rmax, dcx, dcy, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cx, dcx, (rmax + 1) * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cy, dcy, (rmax + 1) * sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    return cuda_err(e);
+}
+
 int lat_correlation_sampled(lat_t* h, uint32_t R, const uint32_t* r, uint32_t nr, int64_t* cx, int64_t* cy)
 {
     const NvtxRange range("lat_correlation_sampled");
@@ -461,6 +475,15 @@ int lat_hash(lat_t* h, uint64_t* out)
     cudaError_t e = launch_hash(h->p.model, h->spins(), h->p.L, h->W, d, h->ls.sms, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_err(e);
+}
+
+int lat_hash_async(lat_t* h, uint64_t* out)
+{
+    if (!h || !out) return LAT_EINVAL;
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(h->misc() + 16);
+    cudaError_t e = launch_hash(h->p.model, h->spins(), h->p.L, h->W, d, h->ls.sms, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream);
     return cuda_err(e);
 }
 

@@ -263,6 +263,13 @@ struct lat_runner {
     size_t host_bytes;
     cudaGraphExec_t graph;
     bool have_graph;
+    // a run submitted and not yet collected
+    bool pending = false;
+    std::vector<lat_t*> pend_lat;
+    std::vector<uint32_t> pend_ns;
+    long long* pend_hobs = nullptr;
+    MultiCtl* pend_hctl = nullptr;
+    cudaEvent_t dep_event = nullptr;  // orders the runner's stream after work on a handle's other stream
 
     MultiDesc* d_desc() const { return reinterpret_cast<MultiDesc*>(buf + lay.desc); }
     uint32_t* d_tile_prefix() const { return reinterpret_cast<uint32_t*>(buf + lay.tile_prefix); }
@@ -435,11 +442,11 @@ static bool runner_maps_ok(const MultiDesc* hd, const uint32_t* htp, const unsig
     return true;
 }
 
-int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
-                   lat_obs* const* per_sweep)
+int lat_runner_submit(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps)
 {
-    const NvtxRange range("lat_runner_run");
+    const NvtxRange range("lat_runner_submit");
     if (!R || !lattices || !nsweeps || n == 0 || n > R->cap) return LAT_EINVAL;
+    if (R->pending) return LAT_ESTATE;
     for (uint32_t i = 0; i < n; ++i) {
         if (!lattices[i] || nsweeps[i] > R->max_sweeps) return LAT_EINVAL;
         if (lattices[i]->p.L > (1u << 19)) return LAT_EINVAL;  // items of one phase must fit in 31 bits
@@ -447,9 +454,24 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
         for (uint32_t j = 0; j < i; ++j)
             if (lattices[j] == lattices[i]) return LAT_EINVAL;  // a lattice may appear once per run
     }
-    // every handle's earlier work must be complete before the runner's stream touches it
-    for (uint32_t i = 0; i < n; ++i)
-        if (cudaStreamSynchronize(lattices[i]->stream) != cudaSuccess) return LAT_ECUDA;
+    // every handle's earlier work must be complete before the runner's stream
+    // touches it: stream order covers handles on the runner's own stream; the
+    // runner's stream waits (on the device) for the last work of any other
+    if (!R->dep_event &&
+        cudaEventCreateWithFlags(&R->dep_event, cudaEventDisableTiming) != cudaSuccess) {
+        R->dep_event = nullptr;
+        return LAT_ECUDA;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        cudaStream_t hs = lattices[i]->stream;
+        if (hs == R->stream) continue;
+        bool seen = false;
+        for (uint32_t j = 0; j < i && !seen; ++j) seen = lattices[j]->stream == hs;
+        if (seen) continue;
+        if (cudaEventRecord(R->dep_event, hs) != cudaSuccess ||
+            cudaStreamWaitEvent(R->stream, R->dep_event, 0) != cudaSuccess)
+            return LAT_ECUDA;
+    }
 
     // order: descending sweep count (stable), so active lattices of a phase are a prefix
     std::vector<uint32_t> order(n);
@@ -567,36 +589,57 @@ int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const ui
     if (e == cudaSuccess && maxs > 0) e = cudaMemsetAsync(R->d_obs(), 0, obs_words * sizeof(long long), st);
     if (e == cudaSuccess && K > 0) e = R->have_graph ? cudaGraphLaunch(R->graph, st) : enqueue_run(R, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hctl, R->d_ctl(), sizeof(MultiCtl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return LAT_ECUDA;
-    if (hctl->error) return LAT_ETIMEDOUT;
-
-    if (per_sweep && maxs > 0) {
-        // one copy of the whole record region into pinned staging
+    // one copy of the whole record region into pinned staging
+    if (e == cudaSuccess && maxs > 0)
         e = cudaMemcpyAsync(hobs, R->d_obs(), obs_words * sizeof(long long), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return LAT_ECUDA;
-        for (uint32_t i = 0; i < n; ++i) {
-            if (!per_sweep[i] || nsweeps[i] == 0) continue;
-            const long long* r = hobs + (size_t)i * R->max_sweeps * kObsWords;
-            for (uint32_t s = 0; s < nsweeps[i]; ++s) {
-                lat_obs& o = per_sweep[i][s];
-                o.M = r[(size_t)s * kObsWords + kObsM];
-                o.B = r[(size_t)s * kObsWords + kObsB];
-                o.Q = r[(size_t)s * kObsWords + kObsQ];
-                o.draws = (uint64_t)r[(size_t)s * kObsWords + kObsDraws];
-                o.sweep = lattices[i]->next_sweep + s + 1;
-            }
+    if (e != cudaSuccess) return LAT_ECUDA;
+    R->pending = true;
+    R->pend_lat.assign(lattices, lattices + n);
+    R->pend_ns.assign(nsweeps, nsweeps + n);
+    R->pend_hobs = hobs;
+    R->pend_hctl = hctl;
+    return LAT_OK;
+}
+
+int lat_runner_collect(lat_runner_t* R, lat_obs* const* per_sweep)
+{
+    const NvtxRange range("lat_runner_collect");
+    if (!R) return LAT_EINVAL;
+    if (!R->pending) return LAT_ESTATE;
+    R->pending = false;
+    if (cudaStreamSynchronize(R->stream) != cudaSuccess) return LAT_ECUDA;
+    if (R->pend_hctl->error) return LAT_ETIMEDOUT;
+    const uint32_t n = (uint32_t)R->pend_lat.size();
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!per_sweep || !per_sweep[i] || R->pend_ns[i] == 0) continue;
+        const long long* r = R->pend_hobs + (size_t)i * R->max_sweeps * kObsWords;
+        for (uint32_t s = 0; s < R->pend_ns[i]; ++s) {
+            lat_obs& o = per_sweep[i][s];
+            o.M = r[(size_t)s * kObsWords + kObsM];
+            o.B = r[(size_t)s * kObsWords + kObsB];
+            o.Q = r[(size_t)s * kObsWords + kObsQ];
+            o.draws = (uint64_t)r[(size_t)s * kObsWords + kObsDraws];
+            o.sweep = R->pend_lat[i]->next_sweep + s + 1;
         }
     }
-    for (uint32_t i = 0; i < n; ++i) lattices[i]->next_sweep += nsweeps[i];
+    for (uint32_t i = 0; i < n; ++i) R->pend_lat[i]->next_sweep += R->pend_ns[i];
     return LAT_OK;
+}
+
+int lat_runner_run(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps,
+                   lat_obs* const* per_sweep)
+{
+    const NvtxRange range("lat_runner_run");
+    const int rc = lat_runner_submit(R, lattices, n, nsweeps);
+    if (rc != LAT_OK) return rc;
+    return lat_runner_collect(R, per_sweep);
 }
 
 int lat_runner_destroy(lat_runner_t* R)
 {
     if (!R) return LAT_OK;
     cudaError_t e = cudaStreamSynchronize(R->stream);
+    if (R->dep_event) cudaEventDestroy(R->dep_event);
     if (R->have_graph) cudaGraphExecDestroy(R->graph);
     if (R->host) cudaFreeHost(R->host);
     if (R->owns) {

@@ -44,6 +44,26 @@ class JobResult:
         return self.completed - self.job.arrival
 
 
+class Deferred:
+    """A result the device writes asynchronously (a correlation or a final
+    hash): settle() fills .value once the engine's stream has passed the
+    work, and returns it."""
+
+    __slots__ = ("value", "_fill")
+
+    def __init__(self, fill):
+        self.value, self._fill = None, fill
+
+    def settle(self):
+        if self._fill is not None:
+            self.value, self._fill = self._fill(), None
+        return self.value
+
+
+def resolve(x):
+    return x.settle() if isinstance(x, Deferred) else x
+
+
 def next_measurement(done: int) -> int:
     """The next power of two strictly above `done` (measurement after 1, 2, 4, ... sweeps)."""
     p = 1
@@ -84,7 +104,13 @@ def plan_step(active, budget_updates: float, max_sweeps: int, policy: str = "fai
 
 
 class GpuEngine:
-    """The device side: lattices in torch-owned buffers, one runner."""
+    """The device side: lattices in torch-owned buffers, one runner, all on
+    the runner's stream.  A step is submitted and collected; the
+    measurements and final hashes of a step are only enqueued (results in
+    page-locked buffers, returned as Deferred), so the device runs them while
+    the host plans the next step, and the next step's collect, which waits
+    for the stream, settles them.  A finished lattice is closed after that
+    collect."""
 
     def __init__(self, max_jobs: int, max_step_sweeps: int, rmax_cap: int = 1024, tiles=None):
         from . import binding as b
@@ -95,6 +121,31 @@ class GpuEngine:
                 self.runner.set_tile(m, L, t)
         self.rmax_cap = rmax_cap
         self.launches = 0  # kernels launched: quench, runner runs, correlation, hash
+        self.pending = []   # Deferred results written by enqueued work
+        self.retired = []   # finished lattices, closed once their hash has landed
+        self.pool = {}      # page-locked int64 buffers by length, for reuse
+
+    def _pinned(self, n: int):
+        import torch
+        free = self.pool.setdefault(n, [])
+        t = free.pop() if free else torch.empty(n, dtype=torch.int64, pin_memory=True)
+        return t, t.numpy()
+
+    def _release_pinned(self, n: int, t) -> None:
+        self.pool[n].append(t)
+
+    def settle(self) -> None:
+        """Wait for the stream, fill every pending result and close retired lattices."""
+        self.runner.stream.synchronize()
+        self._settled()
+
+    def _settled(self) -> None:
+        for d in self.pending:
+            d.settle()
+        self.pending = []
+        for h in self.retired:
+            h.close()
+        self.retired = []
 
     def footprint(self, job) -> int:
         return self.b.lat_footprint(self.b.make_params(job.model, job.L, job.T, job.seed, Delta=job.Delta))
@@ -105,28 +156,50 @@ class GpuEngine:
 
     def advance(self, handles, nsweeps):
         self.launches += 1 if any(nsweeps) else 0
-        return self.runner.run(handles, nsweeps)
+        self.runner.submit(handles, nsweeps)
+        obs = self.runner.collect(nsweeps)
+        self._settled()  # the collect waited for the stream: earlier measurements and hashes are in
+        return obs
 
     def measure(self, h):
         rmax = min(h.L // 2, self.rmax_cap)
         self.launches += 1 if rmax <= 32 else 2
-        return h.correlation(rmax)
+        n = 2 * (rmax + 1)
+        t, buf = self._pinned(n)
+        self.b.lat_correlation_async(h.handle, rmax, buf[:rmax + 1], buf[rmax + 1:])
+
+        def fill():
+            out = (buf[:rmax + 1].copy(), buf[rmax + 1:].copy())
+            self._release_pinned(n, t)
+            return out
+        d = Deferred(fill)
+        self.pending.append(d)
+        return d
 
     def sweep(self, h, n: int):
         """The one-lattice path (sequential baseline): two phase launches per sweep."""
         self.launches += 2 * n
         return h.sweep(n)
 
-    def finish(self, h) -> int:
+    def finish(self, h):
         self.launches += 1
-        v = h.hash()
-        h.close()
-        return v
+        t, buf = self._pinned(1)
+        self.b.lat_hash_async(h.handle, buf.view(np.uint64))
+
+        def fill():
+            v = int(buf.view(np.uint64)[0])
+            self._release_pinned(1, t)
+            return v
+        d = Deferred(fill)
+        self.pending.append(d)
+        self.retired.append(h)
+        return d
 
     def abort(self, h) -> None:
         h.close()
 
     def close(self):
+        self.settle()
         self.runner.close()
 
 
@@ -259,8 +332,15 @@ class Server:
                     continue
                 keep.append(a)
             active = keep
+        settle = getattr(self.engine, "settle", None)
+        if settle is not None:
+            settle()
         self.wall = self.clock() - t0
-        return [results[j.id] for j in jobs]
+        out = [results[j.id] for j in jobs]
+        for r in out:
+            r.corr = {t: resolve(v) for t, v in r.corr.items()}
+            r.final_hash = resolve(r.final_hash)
+        return out
 
 
 def run_sequential(engine, jobs, clock=time.perf_counter, sleep=time.sleep):
@@ -283,6 +363,11 @@ def run_sequential(engine, jobs, clock=time.perf_counter, sleep=time.sleep):
             if (done & (done - 1)) == 0:
                 r.corr[done] = engine.measure(h)
         r.final_hash = engine.finish(h)
+        settle = getattr(engine, "settle", None)
+        if settle is not None:   # the job's results are in and its lattice is released
+            settle()
+        r.corr = {t: resolve(v) for t, v in r.corr.items()}
+        r.final_hash = resolve(r.final_hash)
         r.completed = clock() - t0
         out.append(r)
     return out

@@ -141,3 +141,47 @@ def test_runner_counters_cross_the_32_bit_boundary(gpu):
     ref_obs = [r.sweep(2) for r in refs]
     _check_same(lats, refs, obs, ref_obs)
     runner.close()
+
+
+def test_submit_collect_and_async_measurements(gpu):
+    """lat_runner_submit / lat_runner_collect give what lat_runner_run gives;
+    lat_correlation_async and lat_hash_async, enqueued behind a run on the
+    runner's stream, give what the synchronous calls give once collected; a
+    handle on another stream is ordered before the run by a device-side wait;
+    and the call sequence is checked (LAT_ESTATE)."""
+    import torch
+    runner = b.Runner(8, 16)
+    side = torch.cuda.Stream()
+    jobs = [(0, 512, TC, 0.0, 51), (1, 256, 1.4, 1.0, 52), (0, 1024, 0.9 * TC, 0.0, 53)]
+    lats = [b.Lattice(m, L, T, s, Delta=D, stream=runner.stream) for (m, L, T, D, s) in jobs[:2]]
+    lats.append(b.Lattice(*[jobs[2][i] for i in (0, 1, 2, 4)], Delta=0.0, stream=side))
+    refs = _make(jobs)
+    ns = [6, 9, 4]
+    with pytest.raises(b.LatError) as e:
+        runner.collect(ns)
+    assert e.value.code == b.LAT_ESTATE
+    runner.submit(lats, ns)
+    with pytest.raises(b.LatError) as e:
+        runner.submit(lats, ns)
+    assert e.value.code == b.LAT_ESTATE
+    obs = runner.collect(ns)
+    ref_obs = [r.sweep(k) for r, k in zip(refs, ns)]
+    _check_same(lats, refs, obs, ref_obs)
+    # measurements enqueued behind the next run, read after its collect
+    runner.submit(lats[:2], [3, 5])
+    pinned = [torch.zeros(2 * 257, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    hashes = torch.zeros(2, dtype=torch.int64, pin_memory=True)
+    for lt, buf in zip(lats[:2], pinned):
+        a = buf.numpy()
+        b.lat_correlation_async(lt.handle, 128, a[:129], a[129:258])
+    for i, lt in enumerate(lats[:2]):
+        b.lat_hash_async(lt.handle, hashes.numpy().view(np.uint64)[i:i + 1])
+    runner.collect([3, 5])
+    runner.stream.synchronize()
+    for i, (lt, r, k) in enumerate(zip(lats[:2], refs[:2], [3, 5])):
+        r.sweep(k, record=False)
+        rx, ry = r.correlation(128)
+        a = pinned[i].numpy()
+        assert np.array_equal(a[:129], rx) and np.array_equal(a[129:258], ry)
+        assert int(hashes.numpy().view(np.uint64)[i]) == r.hash() == lt.hash()
+    runner.close()
