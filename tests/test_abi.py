@@ -152,3 +152,17 @@ def test_static_correlation_checks_arguments_before_any_device_call():
                                 (0, 256, None, 4)]:
         assert f(model, L, ptr, rmax, px, py, None) == b.LAT_EINVAL, (model, L, ptr, rmax)
     assert f(0, 256, fake, 4, None, py, None) == b.LAT_EINVAL
+
+
+def test_entry_points_check_null_arguments_without_a_device():
+    """Calls that take a handle refuse a NULL one (and the runner's halves a
+    NULL runner) with LAT_EINVAL, before any device work."""
+    lib = b.load()
+    P = ctypes.c_void_p
+    buf = np.zeros(16, dtype=np.int64)
+    ptr = buf.ctypes.data_as(P)
+    for name, args in [("lat_sweep_sd", [None, 1, None, ptr]), ("lat_correlation_async", [None, 4, ptr, ptr]),
+                       ("lat_hash_async", [None, ptr]), ("lat_runner_submit", [None, None, 1, ptr]),
+                       ("lat_runner_collect", [None, None]), ("lat_runner_set_counter_base", [None, 0]),
+                       ("lat_probe_rates", [None, None])]:
+        assert getattr(lib, name)(*args) == b.LAT_EINVAL, name
