@@ -418,16 +418,21 @@ def end_to_end(b, mk, stream, device, dist, wl, K, world, final_hash):
     barrier(dist, device)
     t0 = time.perf_counter()
     b.lat_set_state(lat.handle, host_np)
-    _, _, _, _, nobs, corr_rows, _, _ = run_job(lat, K, wl, stream)
+    t1 = time.perf_counter()
+    sweep_ms, _, _, _, nobs, corr_rows, corr_s, _ = run_job(lat, K, wl, stream)
+    t2 = time.perf_counter()
     b.lat_get_state(lat.handle, nbytes, host_np)
     torch.cuda.synchronize(device)
-    e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
+    t3 = time.perf_counter()
+    e2e_secs = reduce_max(dist, t3 - t0, device)
     assert lat.hash() == final_hash, "end-to-end run diverged from the device-resident run"
     lat.close()
     d2h = nbytes + nobs * 40 + corr_rows * (2 * 8 + (4 + 8 if wl.get("protocol") else 0))
     L2 = float(wl["L"]) ** 2
     return {"value": whole_job(L2 * K, world, e2e_secs), "unit": UNIT,
-            "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K}
+            "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": d2h / K,
+            "seconds": {"upload": t1 - t0, "job": t2 - t1, "download": t3 - t2,
+                        "job_kernels_by_events": sweep_ms / 1e3 + corr_s}}
 
 
 def finish(args, wl, rank, world, K, W, value, max_secs, ncorr, nlaunch, roofline, e2e, clocks, dist, batched=None):

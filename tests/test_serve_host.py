@@ -249,3 +249,56 @@ def test_cancellation_while_waiting_running_or_before_arrival():
             assert r.status == "done"
             _check_done(r)
     assert eng.live == 0
+
+
+class DeferringEngine(FakeEngine):
+    """An engine whose measurements and final hashes arrive later (as the GPU
+    engine's do): they are Deferred until the next step or settle()."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.pending = []
+        self.settles = 0
+
+    def measure(self, h):
+        v = super().measure(h)
+        d = serve.Deferred(lambda: v)
+        self.pending.append(d)
+        return d
+
+    def finish(self, h):
+        v = super().finish(h)
+        d = serve.Deferred(lambda: v)
+        self.pending.append(d)
+        return d
+
+    def advance(self, handles, nsweeps):
+        out = super().advance(handles, nsweeps)
+        for d in self.pending:
+            d.settle()
+        self.pending = []
+        return out
+
+    def sweep(self, h, n):
+        return self.advance([h], [n])[0]
+
+    def settle(self):
+        self.settles += 1
+        for d in self.pending:
+            d.settle()
+        self.pending = []
+
+
+def test_deferred_results_are_resolved_in_every_job():
+    clock = Clock()
+    eng = DeferringEngine(clock)
+    srv = serve.Server(eng, mem_budget=600_000, max_batch=16, step_updates=5e6, max_step_sweeps=64,
+                       clock=clock, sleep=clock.sleep)
+    res = srv.run(_jobs(40, 21))
+    assert eng.settles >= 1 and not eng.pending
+    for r in res:
+        assert r.final_hash == r.job.id * 7 + r.job.sweeps
+        assert all(isinstance(v, tuple) and int(v[0][0]) == t for t, v in r.corr.items())
+    seq = serve.run_sequential(DeferringEngine(clock), _jobs(10, 22), clock=clock, sleep=clock.sleep)
+    for r in seq:
+        assert isinstance(r.final_hash, int) and all(isinstance(v, tuple) for v in r.corr.values())
