@@ -566,40 +566,65 @@ def served_bench(args):
         e = serve.GpuEngine(8, 8)
         serve.Server(e, 1 << 30, 8).run(warm)
         e.close()
-    eng = serve.GpuEngine(args.max_batch, args.step_sweeps, tiles=tiles)
-    srv = serve.Server(eng, mem_budget=int(args.mem_gib * (1 << 30)), max_batch=args.max_batch,
-                       step_updates=args.step_updates, max_step_sweeps=args.step_sweeps, policy=args.policy)
-    sampler = ClockSampler(gpu_id_for(local)).start()
-    barrier(dist, device)
-    res = srv.run(jobs)
-    clocks = sampler.stop()
-    srv_launches = eng.launches
-    eng.close()
-    s_srv = serve.summarize(res, srv.wall)
+    config = {"workload": "served: first %d jobs of the Poisson stream (%.0f jobs/s, Ising p=0.7 / "
+                          "Blume-Capel Delta in {0.5,1,1.5}, L=2^8..2^14, T=[0.7,1.3] Tc_ref, "
+                          "sweeps log-uniform 10..10000, C(r<=min(L/2,1024)) at sweeps 2^k), "
+                          "seed 20250" % (len(jobs), args.rate),
+              "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch, "policy": args.policy,
+              "step_updates": args.step_updates, "parallelism": "replicas" if world > 1 else "single"}
+    if args.served_part in ("both", "served"):
+        eng = serve.GpuEngine(args.max_batch, args.step_sweeps, tiles=tiles)
+        srv = serve.Server(eng, mem_budget=int(args.mem_gib * (1 << 30)), max_batch=args.max_batch,
+                           step_updates=args.step_updates, max_step_sweeps=args.step_sweeps, policy=args.policy)
+        sampler = ClockSampler(gpu_id_for(local)).start()
+        barrier(dist, device)
+        res = srv.run(jobs)
+        clocks = sampler.stop()
+        srv_launches = eng.launches
+        eng.close()
+        served = dict(serve.summarize(res, srv.wall), steps=srv.steps, peak_batch=srv.peak_batch,
+                      peak_mem=srv.peak_mem)
+        wall = reduce_max(dist, srv.wall, device)
+        srv_digests = [serve.digest(r) for r in res]
+        if args.served_part == "served":
+            # the sequential run follows in another process (it compares these digests)
+            if rank == 0 and args.digests:
+                with open(args.digests, "w") as f:
+                    json.dump({"config": config, "served": served, "wall": wall, "clocks": clocks,
+                               "gpu_launches": srv_launches, "ids": [r.job.id for r in res],
+                               "digests": srv_digests}, f)
+            if rank == 0:
+                print(json.dumps({"served_part": "served", "config": config, "served": served, "clocks": clocks,
+                                  "gpu_launches": srv_launches, "digests_file": args.digests}), flush=True)
+            if dist is not None:
+                dist.destroy_process_group()
+            return
+    else:
+        with open(args.digests) as f:
+            rec = json.load(f)
+        assert rec["config"] == config, "the digests were written for another served workload"
+        served, wall, clocks, srv_launches = rec["served"], rec["wall"], rec["clocks"], rec["gpu_launches"]
+        srv_digests = rec["digests"]
     seq_eng = serve.GpuEngine(1, 1)
+    seq_sampler = ClockSampler(gpu_id_for(local)).start()
     barrier(dist, device)
     t0 = time.perf_counter()
     seq = serve.run_sequential(seq_eng, jobs)
     seq_wall = time.perf_counter() - t0
+    seq_clocks = seq_sampler.stop()
     seq_launches = seq_eng.launches
     seq_eng.close()
     s_seq = serve.summarize(seq, seq_wall)
-    exact = all(serve.same_results(a, b) for a, b in zip(res, seq))
-    wall = reduce_max(dist, srv.wall, device)
-    value = whole_job(s_srv["updates"], world, wall)
+    exact = len(seq) == len(srv_digests) and all(serve.digest(r) == d for r, d in zip(seq, srv_digests))
+    value = whole_job(served["updates"], world, wall)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(jobs),
                 "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": "served: first %d jobs of the Poisson stream (%.0f jobs/s, Ising p=0.7 / "
-                                       "Blume-Capel Delta in {0.5,1,1.5}, L=2^8..2^14, T=[0.7,1.3] Tc_ref, "
-                                       "sweeps log-uniform 10..10000, C(r<=min(L/2,1024)) at sweeps 2^k), "
-                                       "seed 20250" % (len(jobs), args.rate),
-                           "mem_budget_gib": args.mem_gib, "max_batch": args.max_batch, "policy": args.policy,
-                           "step_updates": args.step_updates, "parallelism": "replicas" if world > 1 else "single"},
-                "served": dict(s_srv, steps=srv.steps, peak_batch=srv.peak_batch, peak_mem=srv.peak_mem),
-                "sequential_plain": dict(s_seq, gpu_launches=seq_launches), "bit_exact": exact, "clocks": clocks,
-                "gpu_launches": srv_launches}
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config,
+                "served": served, "sequential_plain": dict(s_seq, gpu_launches=seq_launches, clocks=seq_clocks),
+                "bit_exact": exact, "bit_exact_by": "SHA-256 of every job's records, C(r) and final hash",
+                "clocks": clocks, "gpu_launches": srv_launches,
+                "served_part": args.served_part}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -661,6 +686,10 @@ def main(argv=None):
     ap.add_argument("--step-sweeps", type=int, default=16, help="served: most sweeps per job per step")
     ap.add_argument("--policy", choices=["fair", "srpt"], default="srpt",
                     help="served: per-step sweep plan (equal quotas, or shortest remaining work first)")
+    ap.add_argument("--served-part", choices=["both", "served", "sequential"], default="both",
+                    help="served: run both paths, or one of them (the sequential part compares the digests the "
+                         "served part wrote, for streams too long for one process)")
+    ap.add_argument("--digests", default=None, help="served: file of per-job result digests (written / read)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="oracle CPU-baseline budget; 0 skips it (profiling runs)")
     ap.add_argument("--L", type=int, default=None, help="override the linear size (small profiling cases)")

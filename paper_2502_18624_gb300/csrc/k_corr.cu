@@ -21,13 +21,16 @@
 //    strip.
 // In both, the window's slots rotate by full unrolling (slot (i+k) % NQ
 // holds the element at offset k), so no register moves are needed.
+#include <type_traits>
+
 #include "lat_internal.cuh"
 
 namespace latk {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kXWarpsMax = 8;     // word-offset groups per x block (one per warp)
+constexpr int kXGroupsMax = 8;    // word-offset groups per x block
+constexpr int kXWarpsMax = 16;    // warps per x block: groups x row parts
 constexpr int kYWarps = 8;        // distance groups per y block
 
 template <int MODEL>
@@ -105,20 +108,22 @@ __device__ __forceinline__ void stage_row32_ext(const void* spins, uint32_t W32,
 template <int MODEL, int NQ>
 __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, uint32_t L, uint32_t rmax,
                                                            uint32_t rows_per_block, long long* cx, uint32_t ext,
-                                                           uint32_t nbuf, uint32_t one)
+                                                           uint32_t nbuf, uint32_t gpb, uint32_t span, uint32_t one)
 {
     // One row at a time is worked on by the whole block, extended
     // periodically to `ext` words (enough for the largest offset any warp of
     // the grid reads), while the next row is copied into the other of two
     // buffers (nbuf = 2; with nbuf = 1, for rows too long for two buffers, the
-    // next row is copied after the block is done with this one); warp g of
-    // the block owns word offsets
-    // q0 = (blockIdx.y * nwarps + g) * NQ .. + NQ - 1.
+    // next row is copied after the block is done with this one).  The block
+    // has gpb offset groups times (warps / gpb) row parts: warp w owns word
+    // offsets q0 = (blockIdx.y * gpb + w % gpb) * NQ .. + NQ - 1 for the row
+    // words [i0, i1) of part w / gpb (span words each), so that several
+    // warps share one staged row even when rmax needs few offset groups.
     extern __shared__ uint32_t sm[];
     const uint32_t W32 = L / 32;
     const int warp = threadIdx.x >> 5, s = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const uint32_t q0 = (blockIdx.y * nwarps + warp) * NQ;
+    const uint32_t q0 = (blockIdx.y * gpb + (uint32_t)warp % gpb) * NQ;
+    const uint32_t i0 = min(W32, ((uint32_t)warp / gpb) * span), i1 = min(W32, i0 + span);
     constexpr int P = Planes<MODEL>::n;
     const uint32_t m2 = 0u - 2u * one;  // -2, for the Blume-Capel opposite-sign pairs
     int acc[NQ];        // Ising: carries of the carry-save sums; Blume-Capel: the sums themselves
@@ -140,57 +145,60 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
         uint32_t win[NQ], wing[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            win[k] = rot_word(row, q0 + k, s);
-            if constexpr (MODEL == 1) wing[k] = rot_word(row + ext, q0 + k, s);
+            win[k] = rot_word(row, q0 + i0 + k, s);
+            if constexpr (MODEL == 1) wing[k] = rot_word(row + ext, q0 + i0 + k, s);
         }
-        uint32_t jn = q0 + NQ;  // i + q0 + NQ: the word entering the window (< ext - 1)
+        uint32_t jn = q0 + NQ + i0;  // i + q0 + NQ: the word entering the window (< ext - 1)
         if constexpr (MODEL == 0) {
             // Words i and i+1 (W32 is even) go through one carry-save step per
             // distance: sum bits stay in ones[k], the carries are counted.
-            for (uint32_t ib = 0; ib < W32; ib += 2 * NQ) {
+            // A group covers words ib .. ib + 2 NQ - 1 (FULL: all below W32);
+            // the entering word of word i is row[q0 + NQ + i].
+            auto group = [&](auto full, uint32_t ib) {
+                constexpr bool FULL = decltype(full)::value;
+                const uint32_t* rw = row + ib;           // row word i = rw[u]
+                const uint32_t* en = row + q0 + NQ + ib; // entering word of word i = en[u]
 #pragma unroll
                 for (int u = 0; u < 2 * NQ; u += 2) {
-                    const uint32_t i = ib + u;
-                    if (i < W32) {
-                        const uint32_t a1 = row[i], a2 = row[i + 1];
+                    if (FULL || ib + u < i1) {
+                        const uint32_t a1 = rw[u], a2 = rw[u + 1];
                         uint32_t x1[NQ];
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
-                        win[u % NQ] = rot_word(row, jn, s);
-                        ++jn;
+                        win[u % NQ] = __funnelshift_r(en[u], en[u + 1], s);
 #pragma unroll
                         for (int k = 0; k < NQ; ++k) {
                             const uint32_t x2 = a2 ^ win[(u + 1 + k) % NQ];
                             acc[k] = mad_acc(acc[k], __popc(csa_carry(ones[k], x1[k], x2)), one);
                             ones[k] = csa_sum(ones[k], x1[k], x2);
                         }
-                        win[(u + 1) % NQ] = rot_word(row, jn, s);
-                        ++jn;
+                        win[(u + 1) % NQ] = __funnelshift_r(en[u + 1], en[u + 2], s);
                     }
                 }
-            }
-            __syncthreads();  // every warp is done with this buffer before it is refilled
-            if (nbuf == 1 && y + 1 < yend) stage_row32_ext<MODEL>(spins, W32, y + 1, ext, sm, threadIdx.x, blockDim.x);
-            continue;
-        }
-        for (uint32_t ib = 0; ib < W32; ib += NQ) {
+            };
+            uint32_t ib = i0;
+            for (; ib + 2 * NQ <= i1; ib += 2 * NQ) group(std::integral_constant<bool, true>{}, ib);
+            if (ib < i1) group(std::integral_constant<bool, false>{}, ib);
+        } else {
+            for (uint32_t ib = i0; ib < i1; ib += NQ) {
 #pragma unroll
-            for (int u = 0; u < NQ; ++u) {
-                const uint32_t i = ib + u;
-                if (i < W32) {
-                    const uint32_t a = row[i];
-                    {
-                        const uint32_t ag = row[ext + i];
+                for (int u = 0; u < NQ; ++u) {
+                    const uint32_t i = ib + u;
+                    if (i < i1) {
+                        const uint32_t a = row[i];
+                        {
+                            const uint32_t ag = row[ext + i];
 #pragma unroll
-                        for (int k = 0; k < NQ; ++k) {
-                            const uint32_t both = a & win[(u + k) % NQ];
-                            acc[k] = mad_acc(acc[k], __popc(both), one);
-                            acc[k] = mad_acc(acc[k], __popc(both & (ag ^ wing[(u + k) % NQ])), m2);
+                            for (int k = 0; k < NQ; ++k) {
+                                const uint32_t both = a & win[(u + k) % NQ];
+                                acc[k] = mad_acc(acc[k], __popc(both), one);
+                                acc[k] = mad_acc(acc[k], __popc(both & (ag ^ wing[(u + k) % NQ])), m2);
+                            }
+                            win[u] = rot_word(row, jn, s);
+                            wing[u] = rot_word(row + ext, jn, s);
                         }
-                        win[u] = rot_word(row, jn, s);
-                        wing[u] = rot_word(row + ext, jn, s);
+                        ++jn;
                     }
-                    ++jn;
                 }
             }
         }
@@ -201,9 +209,10 @@ __global__ void __launch_bounds__(kXWarpsMax * 32) k_corr_x(const void* spins, u
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         const uint32_t r = 32u * (q0 + k) + s;
-        if (r <= rmax && rows) {
+        if (r <= rmax && rows && i1 > i0) {
             const long long mism = 2ll * acc[k] + __popc(ones[k]);  // Ising: disagreeing pairs
-            const long long v = MODEL == 0 ? rows * (long long)L - 2ll * mism : (long long)acc[k];
+            // Ising: this warp's pairs are rows x 32 (i1 - i0) sites, each 1 - 2 [unequal]
+            const long long v = MODEL == 0 ? rows * 32ll * (i1 - i0) - 2ll * mism : (long long)acc[k];
             atomicAdd(reinterpret_cast<unsigned long long*>(cx + r), (unsigned long long)v);
         }
     }
@@ -220,10 +229,14 @@ template <int NQ>
 struct YRing {
     static constexpr uint32_t step = 2 * NQ;  // rows staged per step
     // A step reads ring entries [ys, ys + D + step) while the next step's
-    // entries [ys + D + step, ys + D + 2 step) are copied in: the ring must
-    // hold D + 2 step entries so the two never share a slot.
-    static constexpr uint32_t need = kYWarps * NQ + 2 * step;
-    static constexpr uint32_t rows = need <= 64 ? 64 : (need <= 128 ? 128 : 256);
+    // entries [ys + D + step, ys + D + 2 step) are copied in: with D + 2 step
+    // slots (entry t in slot t mod entries) the two never share a slot.
+    static constexpr uint32_t entries = kYWarps * NQ + 2 * step;
+    // In a step a warp reads the NQ + step consecutive entries from ys + g0.
+    // Slots below `mirror` are stored a second time after the last slot, so
+    // that such a run sits at consecutive addresses whatever slot it starts at.
+    static constexpr uint32_t mirror = NQ + step;
+    static constexpr uint32_t rows = entries + mirror;  // physical rows per plane
 };
 
 // Asynchronous copy of word j of row y into shared memory: Ising to dn;
@@ -266,8 +279,9 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
 {
     extern __shared__ uint32_t sm[];
     constexpr int P = Planes<MODEL>::n;
-    constexpr uint32_t R = YRing<NQ>::rows;  // ring rows (power of two)
-    constexpr uint32_t D = kYWarps * NQ;     // distances per block
+    constexpr uint32_t RN = YRing<NQ>::entries, RM = YRing<NQ>::mirror, RP = YRing<NQ>::rows;
+    constexpr uint32_t D = kYWarps * NQ;  // distances per block
+    constexpr uint32_t S = YRing<NQ>::step;
     const uint32_t W32 = L / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Block b covers distance chunk b % chunks of strip (b / chunks) % strips
@@ -282,14 +296,23 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
     const uint32_t H = min(rows_per_block, L - y0);  // even: L and rows_per_block are even
     const uint32_t r0 = chunk * D;
     const uint32_t m2 = 0u - 2u * one;
-    uint32_t* ring = sm;                // R x 32 words per plane
-    uint32_t* arow = sm + R * 32 * P;   // two buffers of 2 NQ x 32 words per plane
+    uint32_t* ring = sm;                // RP x 32 words per plane
+    uint32_t* arow = sm + RP * 32 * P;  // two buffers of S x 32 words per plane
 
     // Lattice row of ring entry t is (y0 + r0 + t) mod L (staging only, so a
     // plain modulo is cheap next to the pair work).
     const uint32_t rb = (uint32_t)(((uint64_t)y0 + r0) % L);
     auto brow = [L, rb](uint32_t t) { return (uint32_t)(((uint64_t)rb + t) % L); };
-    constexpr uint32_t S = YRing<NQ>::step;
+    // Column c of ring entry t: slot t mod RN, and again at RN + slot when
+    // the slot is below RM.
+    auto stage_ring = [&](uint32_t t, uint32_t c) {
+        const uint32_t slot = t % RN, yb = brow(t);
+        stage_strip_word<MODEL>(spins, W32, yb, j0 + c, c < tw, ring + slot * 32 + c,
+                                ring + RP * 32 + slot * 32 + c);
+        if (slot < RM)
+            stage_strip_word<MODEL>(spins, W32, yb, j0 + c, c < tw, ring + (RN + slot) * 32 + c,
+                                    ring + RP * 32 + (RN + slot) * 32 + c);
+    };
     // Copies for the step at ys: A rows ys .. ys+S-1 into buffer b, ring
     // entries D+ys .. D+ys+S-1.
     auto stage_step = [&](uint32_t ys, uint32_t b) {
@@ -301,17 +324,11 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
                 stage_strip_word<MODEL>(spins, W32, ya, j0 + c, c < tw && ys + rr < H, ab + rr * 32 + c,
                                         ab + S * 32 + rr * 32 + c);
             } else {
-                const uint32_t tb = D + ys + rr;
-                stage_strip_word<MODEL>(spins, W32, brow(tb), j0 + c, c < tw, ring + (tb % R) * 32 + c,
-                                        ring + R * 32 + (tb % R) * 32 + c);
+                stage_ring(D + ys + rr, c);
             }
         }
     };
-    for (uint32_t t = threadIdx.x; t < D * 32; t += blockDim.x) {  // ring entries 0 .. D-1
-        const uint32_t rr = t / 32, c = t % 32;
-        stage_strip_word<MODEL>(spins, W32, brow(rr), j0 + c, c < tw, ring + (rr % R) * 32 + c,
-                                ring + R * 32 + (rr % R) * 32 + c);
-    }
+    for (uint32_t t = threadIdx.x; t < D * 32; t += blockDim.x) stage_ring(t / 32, t % 32);  // entries 0 .. D-1
     stage_step(0, 0);
     cp_async_commit();
 
@@ -321,43 +338,38 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
     uint32_t win[NQ], wing[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) acc[k] = 0, ones[k] = 0;
-    for (uint32_t ys = 0, it = 0; ys < H; ys += S, ++it) {
-        const uint32_t* ab = arow + (it & 1u) * S * 32 * P;
-        if (ys + S < H) stage_step(ys + S, (it & 1u) ^ 1u);  // the next step, while this one runs
-        cp_async_commit();
-        cp_async_wait1();  // this step's copies have landed
-        __syncthreads();
-        // window slot k holds ring entry ys + g0 + k at the start of the step
+    // One step of S rows: window slot k holds entry ys + g0 + k at its start,
+    // and entry ys + g0 + j sits at rp[j * 32] (rp[RP * 32 + j * 32] for the g
+    // plane).  FULL: all S rows of the step are in the segment.
+    auto run_step = [&](auto full, uint32_t ys, const uint32_t* ab, const uint32_t* rp) {
+        constexpr bool FULL = decltype(full)::value;
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            const uint32_t tb = ys + g0 + k;
-            win[k] = ring[(tb % R) * 32 + lane];
-            if constexpr (P == 2) wing[k] = ring[R * 32 + (tb % R) * 32 + lane];
+            win[k] = rp[k * 32];
+            if constexpr (P == 2) wing[k] = rp[RP * 32 + k * 32];
         }
         if constexpr (MODEL == 0) {
 #pragma unroll
             for (int u = 0; u < (int)S; u += 2) {
-                if (ys + u < H) {  // then ys + u + 1 < H too (H is even)
+                if (FULL || ys + u < H) {  // then ys + u + 1 < H too (H is even)
                     const uint32_t a1 = ab[u * 32 + lane], a2 = ab[(u + 1) * 32 + lane];
                     uint32_t x1[NQ];
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) x1[k] = a1 ^ win[(u + k) % NQ];
-                    uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
-                    win[u % NQ] = ring[(tb % R) * 32 + lane];
+                    win[u % NQ] = rp[(NQ + u) * 32];  // the entry entering this warp's window
 #pragma unroll
                     for (int k = 0; k < NQ; ++k) {
                         const uint32_t x2 = a2 ^ win[(u + 1 + k) % NQ];
                         acc[k] = mad_acc(acc[k], __popc(csa_carry(ones[k], x1[k], x2)), one);
                         ones[k] = csa_sum(ones[k], x1[k], x2);
                     }
-                    tb += 1;
-                    win[(u + 1) % NQ] = ring[(tb % R) * 32 + lane];
+                    win[(u + 1) % NQ] = rp[(NQ + u + 1) * 32];
                 }
             }
         } else {
 #pragma unroll
             for (int u = 0; u < (int)S; ++u) {
-                if (ys + u < H) {
+                if (FULL || ys + u < H) {
                     const uint32_t a = ab[u * 32 + lane];
                     const uint32_t ag = ab[S * 32 + u * 32 + lane];
 #pragma unroll
@@ -366,12 +378,21 @@ __global__ void __launch_bounds__(kYWarps * 32) k_corr_y(const void* spins, uint
                         acc[k] = mad_acc(acc[k], __popc(both), one);
                         acc[k] = mad_acc(acc[k], __popc(both & (ag ^ wing[(u + k) % NQ])), m2);
                     }
-                    const uint32_t tb = ys + u + g0 + NQ;  // ring entry entering this warp's window
-                    win[u % NQ] = ring[(tb % R) * 32 + lane];
-                    wing[u % NQ] = ring[R * 32 + (tb % R) * 32 + lane];
+                    win[u % NQ] = rp[(NQ + u) * 32];
+                    wing[u % NQ] = rp[RP * 32 + (NQ + u) * 32];
                 }
             }
         }
+    };
+    for (uint32_t ys = 0, it = 0; ys < H; ys += S, ++it) {
+        const uint32_t* ab = arow + (it & 1u) * S * 32 * P;
+        if (ys + S < H) stage_step(ys + S, (it & 1u) ^ 1u);  // the next step, while this one runs
+        cp_async_commit();
+        cp_async_wait1();  // this step's copies have landed
+        __syncthreads();
+        const uint32_t* rp = ring + ((ys + g0) % RN) * 32 + lane;
+        if (ys + S <= H) run_step(std::integral_constant<bool, true>{}, ys, ab, rp);
+        else run_step(std::integral_constant<bool, false>{}, ys, ab, rp);
         __syncthreads();  // every warp is done with this A buffer before it is refilled
     }
     const bool colok = (uint32_t)lane < tw;
@@ -548,12 +569,18 @@ cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx
 {
     const uint32_t W32 = L / 32;
     const uint32_t groups = (rmax / 32 + 1 + NQ - 1) / NQ;   // word-offset groups of NQ
-    const uint32_t nwarps = groups < (uint32_t)kXWarpsMax ? groups : (uint32_t)kXWarpsMax;
-    const uint32_t gy = (groups + nwarps - 1) / nwarps;
+    const uint32_t gpb = groups < (uint32_t)kXGroupsMax ? groups : (uint32_t)kXGroupsMax;  // groups per block
+    const uint32_t gy = (groups + gpb - 1) / gpb;
+    // row parts: as many warps as fit kXWarpsMax, each part at least 8 groups of 2 NQ words
+    uint32_t parts = kXWarpsMax / gpb;
+    const uint32_t most = W32 / (16 * NQ);
+    parts = parts < most ? parts : (most < 1 ? 1 : most);
+    const uint32_t span = ((W32 + parts - 1) / parts + 2 * NQ - 1) / (2 * NQ) * (2 * NQ);
+    const uint32_t nwarps = gpb * parts;
     // the largest word a warp reads is q0 + NQ + W32 (entering words run
-    // from q0 + NQ for W32 steps, plus the next word of each funnel shift),
-    // with q0 < gy * nwarps * NQ
-    const uint32_t ext = gy * nwarps * NQ + NQ + W32 + 1;
+    // from q0 + NQ + i0 up to word i1 - 1 <= W32 - 1, plus the next word of
+    // each funnel shift), with q0 < gy * gpb * NQ
+    const uint32_t ext = gy * gpb * NQ + NQ + W32 + 1;
     const size_t one_buf = (size_t)ext * Planes<MODEL>::n * sizeof(uint32_t);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -576,7 +603,7 @@ cudaError_t launch_x(const void* spins, uint32_t L, uint32_t rmax, long long* cx
     const uint32_t rmax_rows = (1u << 30) / L;
     rpb = rpb > rmax_rows ? rmax_rows : rpb;
     const dim3 grid((L + rpb - 1) / rpb, gy);
-    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, rpb, cx, ext, nbuf, 1u);
+    k_corr_x<MODEL, NQ><<<grid, nwarps * 32, smem, st>>>(spins, L, rmax, rpb, cx, ext, nbuf, gpb, span, 1u);
     return cudaGetLastError();
 }
 
@@ -584,7 +611,7 @@ template <int MODEL, int NQ>
 cudaError_t launch_y(const void* spins, uint32_t L, uint32_t rmax, long long* cy, int sms, cudaStream_t st)
 {
     const uint32_t W32 = L / 32;
-    const size_t smem = (size_t)(YRing<NQ>::rows + 2 * YRing<NQ>::step) * 32 * Planes<MODEL>::n * sizeof(uint32_t);
+    const size_t smem = (size_t)(YRing<NQ>::rows + 2 * YRing<NQ>::step) * 32 * Planes<MODEL>::n * sizeof(uint32_t);  // ring + two A buffers
     cudaError_t e = cudaFuncSetAttribute(k_corr_y<MODEL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint32_t per_block = kYWarps * NQ;

@@ -388,6 +388,24 @@ def summarize(results, wall: float) -> dict:
     return out
 
 
+def digest(r: JobResult) -> str:
+    """SHA-256 over everything a job returns (status, per-sweep records,
+    C(r) at every measurement point, final hash): two runs of a job are
+    bit-identical iff their digests are equal (up to a hash collision).  Lets
+    the served and the sequential runs be compared across processes."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(r.status.encode())
+    h.update(int(r.final_hash).to_bytes(8, "little"))
+    for o in r.obs:
+        h.update(np.ascontiguousarray(o).tobytes())
+    for t in sorted(r.corr):
+        h.update(int(t).to_bytes(8, "little"))
+        for a in r.corr[t]:
+            h.update(np.ascontiguousarray(a, dtype=np.int64).tobytes())
+    return h.hexdigest()
+
+
 def same_results(a: JobResult, b: JobResult) -> bool:
     """Bit-exact comparison of two runs of one job."""
     oa = np.concatenate(a.obs) if a.obs else np.zeros(0)

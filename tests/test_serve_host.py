@@ -302,3 +302,18 @@ def test_deferred_results_are_resolved_in_every_job():
     seq = serve.run_sequential(DeferringEngine(clock), _jobs(10, 22), clock=clock, sleep=clock.sleep)
     for r in seq:
         assert isinstance(r.final_hash, int) and all(isinstance(v, tuple) for v in r.corr.values())
+
+
+def test_digest_separates_runs_that_differ():
+    clock = Clock()
+    res = serve.run_sequential(DeferringEngine(clock), _jobs(6, 23), clock=clock, sleep=clock.sleep)
+    again = serve.run_sequential(DeferringEngine(clock), _jobs(6, 23), clock=clock, sleep=clock.sleep)
+    assert [serve.digest(r) for r in res] == [serve.digest(r) for r in again]
+    r = res[0]
+    d0 = serve.digest(r)
+    r.final_hash += 1
+    assert serve.digest(r) != d0
+    r.final_hash -= 1
+    t = sorted(r.corr)[0]
+    r.corr[t] = (r.corr[t][0] + 1, r.corr[t][1])
+    assert serve.digest(r) != d0
