@@ -147,6 +147,26 @@ def _pack_planes_fail(orc):
     return _fails(tm.test_pack_matches_packbits, orc, 1, 64)
 
 
+def _window_fails(orc):
+    import test_oracle_window as tw
+    return _fails(tw.test_window_interior_equals_periodic_run, orc, 0, ph.TC, 0.0)
+
+
+def _window_lut_fails(orc):
+    import test_oracle_window as tw
+    return _fails(tw.test_lut_window_interior_equals_periodic_run, orc)
+
+
+def _par_fails(orc):
+    import test_oracle_threads as tt
+    return _fails(tt.test_parallel_sweep_equals_sequential, orc, 0, ph.TC, 0.0)
+
+
+def _par_strip_fails(orc):
+    import test_oracle_threads as tt
+    return _fails(tt.test_parallel_strip_sweep_equals_sequential, orc, 1)
+
+
 MUTATIONS = [
     ("sweep drops the east neighbour",
      "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
@@ -197,6 +217,18 @@ MUTATIONS = [
      "                if (v != 0) words[i] |= bit;\n                if (v == -1) words[n + i] |= bit;",
      "                if (v != 0) words[n + i] |= bit;\n                if (v == -1) words[i] |= bit;",
      _pack_planes_fail),
+    ("window sweep draws with the unwrapped site index",
+     "                *c = or_update_site(model, *c, h, y * L + x, sweep, colour, seed, thr);",
+     "                *c = or_update_site(model, *c, h, (y0 + i) * L + (x0 + j), sweep, colour, seed, thr);",
+     _window_fails),
+    ("lookup-table window sweep takes the word index from the window, not the lattice",
+     "                uint64_t w = y * (L / 64) + x / 64;\n                int k = (int)((x % 64) / 2);\n                int flip;\n                if (agree == 4)\n                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k) & or_lut_bit(seed, tbl, w, sweep, colour, 1, k);\n                else if (agree == 3)\n                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k);\n                else\n                    flip = 1;\n                if (flip) *c",
+     "                uint64_t w = i * (L / 64) + j / 64;\n                int k = (int)((x % 64) / 2);\n                int flip;\n                if (agree == 4)\n                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k) & or_lut_bit(seed, tbl, w, sweep, colour, 1, k);\n                else if (agree == 3)\n                    flip = or_lut_bit(seed, tbl, w, sweep, colour, 0, k);\n                else\n                    flip = 1;\n                if (flip) *c",
+     _window_lut_fails),
+    ("row-parallel sweep skips the last row", "        for (int64_t y = 0; y < (int64_t)L; ++y)\n            or_phase_rows(",
+     "        for (int64_t y = 0; y < (int64_t)L - 1; ++y)\n            or_phase_rows(", _par_fails),
+    ("row-parallel strip sweep starts colour 1 one row early", "        int64_t r_lo = colour == 0 ? 1 : 2;",
+     "        int64_t r_lo = 1;", _par_strip_fails),
 ]
 
 
