@@ -36,7 +36,10 @@ template <int CW, bool OBS, bool SD = false>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __grid_constant__ IsingPhaseArgs a)
 {
     __shared__ uint32_t s_lut[kLutSlots];
+    __shared__ uint8_t s_lutb[kLutBuckets];
     if (threadIdx.x < kLutSlots) s_lut[threadIdx.x] = lut_slot(a.lut, threadIdx.x);
+    __syncthreads();
+    lut_buckets(s_lut, s_lutb);
     __syncthreads();
     const IsingPhase ph{a.spins, a.L, a.W, a.sweep, a.colour, a.thr4, a.thr8, a.mode4, a.mode8};
     const uint64_t nitems = (uint64_t)a.L * (a.W / CW);
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_ising_phase_lut(const __gr
     const int lane = threadIdx.x & 31;
     PhaseAcc acc;
     for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems; item += stride)
-        ising_item_lut<CW, OBS, false, SD>(ph, a.rk, s_lut, item, lane, acc);
+        ising_item_lut<CW, OBS, false, SD, true>(ph, a.rk, s_lut, s_lutb, item, lane, acc);
     flush_acc(OBS ? a.obs : nullptr, a.draws, acc);
     if constexpr (SD) flush_sd(a.sd, acc);
 }

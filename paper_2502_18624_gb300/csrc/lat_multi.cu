@@ -104,10 +104,10 @@ __device__ __forceinline__ void ising_tile(const MultiDesc& d, const uint32_t* s
     if (d.rng == LAT_RNG_TABLE_MODE) {
         if (d.cw == 2) {
             for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x)
-                ising_item_lut<2, OBS, true>(ph, rk, s_lut, it, lane, acc);
+                ising_item_lut<2, OBS, true>(ph, rk, s_lut, nullptr, it, lane, acc);
         } else {
             for (uint64_t it = i0 + threadIdx.x; it < i1; it += blockDim.x)
-                ising_item_lut<1, OBS, true>(ph, rk, s_lut, it, lane, acc);
+                ising_item_lut<1, OBS, true>(ph, rk, s_lut, nullptr, it, lane, acc);
         }
         return;
     }

@@ -321,6 +321,42 @@ __device__ __forceinline__ uint32_t lut_find_spread(const uint32_t* ts, uint32_t
     return js;
 }
 
+// One-lookup form of the same search for kernels that hold a 32 KiB shared
+// table: the top 15 bits of a uniform pick a bucket of 2^17 values.  The
+// table is non-decreasing, so where the index is the same at both ends of a
+// bucket it is the same throughout, and the bucket's byte is its spread4; a
+// bucket that holds a step of the index gets the marker 0xAA (bits that no
+// spread index sets), and a uniform that meets it takes the four-step search.
+// At most 15 of the 2^15 buckets hold a step.
+constexpr int kLutBucketShift = 17;
+constexpr int kLutBuckets = 1 << (32 - kLutBucketShift);
+constexpr uint32_t kLutMarker = 0xAAu;
+
+// Fill the bucket table tb from the spread table ts (all threads of the
+// block; ts must be complete, and tb is complete after the next barrier).
+__device__ __forceinline__ void lut_buckets(const uint32_t* ts, uint8_t* tb)
+{
+    for (int b = threadIdx.x; b < kLutBuckets; b += blockDim.x) {
+        const uint32_t u0 = (uint32_t)b << kLutBucketShift, u1 = u0 | ((1u << kLutBucketShift) - 1u);
+        const uint32_t j0 = lut_find_spread(ts, u0);
+        tb[b] = (uint8_t)(j0 == lut_find_spread(ts, u1) ? j0 : kLutMarker);
+    }
+}
+
+// The spread indices of the four uniforms of one Philox block, in bytes 0..3.
+template <bool BUCKETS>
+__device__ __forceinline__ uint32_t lut_bits4(const uint32_t* ts, const uint8_t* tb, const uint4& r)
+{
+    if constexpr (BUCKETS) {
+        const uint32_t xy = __byte_perm(tb[r.x >> kLutBucketShift], tb[r.y >> kLutBucketShift], 0x40u);
+        const uint32_t zw = __byte_perm(tb[r.z >> kLutBucketShift], tb[r.w >> kLutBucketShift], 0x40u);
+        const uint32_t b4 = __byte_perm(xy, zw, 0x5410u);
+        if (!(b4 & (kLutMarker * 0x01010101u))) return b4;
+    }
+    return lut_find_spread(ts, r.x) | (lut_find_spread(ts, r.y) << 8) | (lut_find_spread(ts, r.z) << 16) |
+           (lut_find_spread(ts, r.w) << 24);
+}
+
 // The paper's lookup-table random bits (section 3.2, LAT_RNG_TABLE): per
 // 64-bit word, four Philox blocks (counters 4w+q, sweep, colour+2) give 16
 // uniforms; each is located in the table s_lut (spread form, kLutSlots
@@ -328,10 +364,11 @@ __device__ __forceinline__ uint32_t lut_find_spread(const uint32_t* ts, uint32_t
 // 8..15 word e1: uniform i gives the bits of the word's active sites 4i ..
 // 4i+3, which sit at bits 8i + 2b (+ the row's colour parity).  A 3-agree
 // site flips iff its e0 bit is set, a 4-agree site iff its e0 and e1 bits
-// are.
-template <int CW, bool OBS, bool CG, bool SD = false>
+// are.  BUCKETS: the uniforms are first looked up in the bucket table
+// s_lutb (lut_buckets).
+template <int CW, bool OBS, bool CG, bool SD = false, bool BUCKETS = false>
 __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundKeys& rk, const uint32_t* s_lut,
-                                               uint64_t item, int lane, PhaseAcc& acc)
+                                               const uint8_t* s_lutb, uint64_t item, int lane, PhaseAcc& acc)
 {
     IsingItem<CW> it;
     ising_classify<CW, OBS, CG, SD>(a, item, lane, false, it);
@@ -345,8 +382,7 @@ __device__ __forceinline__ void ising_item_lut(const IsingPhase& a, const RoundK
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint4 r = philox_site_w4((uint32_t)ctr + (uint32_t)q, pc, rk);
-            const uint32_t b4 = lut_find_spread(s_lut, r.x) | (lut_find_spread(s_lut, r.y) << 8) |
-                                (lut_find_spread(s_lut, r.z) << 16) | (lut_find_spread(s_lut, r.w) << 24);
+            const uint32_t b4 = lut_bits4<BUCKETS>(s_lut, s_lutb, r);
             if (q < 2) e0 |= (uint64_t)b4 << (32 * q);  // uniforms 4q .. 4q+3
             else e1 |= (uint64_t)b4 << (32 * (q - 2));
         }
