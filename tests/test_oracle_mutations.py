@@ -167,6 +167,26 @@ def _par_strip_fails(orc):
     return _fails(tt.test_parallel_strip_sweep_equals_sequential, orc, 1)
 
 
+def _strip_fails(orc):
+    import test_oracle_measure as tm
+    return _fails(tm.test_strip_sweep_equals_full_sweep, orc, 0, 0.0)
+
+
+def _init_rows_fail(orc):
+    import test_oracle_measure as tm
+    return _fails(tm.test_init_rows_equals_full_init, orc, 1)
+
+
+def _corr_x_fails(orc):
+    import test_oracle_measure as tm
+    return _fails(tm.test_correlation_equals_fft, orc, 0, 64)
+
+
+def _magnetisation_fails(orc):
+    import test_oracle_measure as tm
+    return _fails(tm.test_measure_matches_array_form, orc, 1, 5)
+
+
 MUTATIONS = [
     ("sweep drops the east neighbour",
      "s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L];\n                s[site] = or_update_site",
@@ -229,6 +249,14 @@ MUTATIONS = [
      "        for (int64_t y = 0; y < (int64_t)L - 1; ++y)\n            or_phase_rows(", _par_fails),
     ("row-parallel strip sweep starts colour 1 one row early", "        int64_t r_lo = colour == 0 ? 1 : 2;",
      "        int64_t r_lo = 1;", _par_strip_fails),
+    ("strip sweep draws with the strip row instead of the lattice row",
+     "                row[x] = or_update_site(model, row[x], h, y * L + x, sweep, colour, seed, thr);",
+     "                row[x] = or_update_site(model, row[x], h, r * L + x, sweep, colour, seed, thr);", _strip_fails),
+    ("quench rows start one row late", "uint64_t y = (y0 + r) % L;", "uint64_t y = (y0 + r + 1) % L;",
+     _init_rows_fail),
+    ("correlation along x shifted by one extra column", "ax += v * s[y * L + (x + r) % L];",
+     "ax += v * s[y * L + (x + r + 1) % L];", _corr_x_fails),
+    ("magnetisation sums squares", "            M += v;", "            M += v * v;", _magnetisation_fails),
 ]
 
 
