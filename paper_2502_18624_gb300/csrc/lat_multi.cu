@@ -418,30 +418,6 @@ int lat_runner_set_counter_base(lat_runner_t* R, uint64_t base)
     return LAT_OK;
 }
 
-// The maps the persistent kernel indexes with no check of its own: every
-// tile number g < total must resolve to a phase k (phase_base), a lattice
-// r < active[k] (tile_prefix) and a tile t < ntiles[r], and every tile must
-// cover items inside its lattice.  Built on the host from validated input,
-// so a failure here is an internal error (LAT_ESTATE), never a launch.
-static bool runner_maps_ok(const MultiDesc* hd, const uint32_t* htp, const unsigned long long* hpb,
-                           const uint32_t* hact, uint32_t n, uint32_t K)
-{
-    if (htp[0] != 0) return false;
-    for (uint32_t s = 0; s < n; ++s) {
-        const MultiDesc& d = hd[s];
-        if (d.tile_items == 0 || d.tile_items % kMultiThreads != 0 || d.ntiles == 0) return false;
-        if ((uint64_t)d.ntiles * d.tile_items < d.items || (uint64_t)(d.ntiles - 1) * d.tile_items >= d.items)
-            return false;
-        if (htp[s + 1] != htp[s] + d.ntiles) return false;
-    }
-    if (hpb[0] != 0) return false;
-    for (uint32_t k = 0; k < K; ++k) {
-        if (hact[k] == 0 || hact[k] > n || (k > 0 && hact[k] > hact[k - 1])) return false;
-        if (hpb[k + 1] != hpb[k] + htp[hact[k]]) return false;
-    }
-    return true;
-}
-
 int lat_runner_submit(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const uint32_t* nsweeps)
 {
     const NvtxRange range("lat_runner_submit");
@@ -561,7 +537,7 @@ int lat_runner_submit(lat_runner_t* R, lat_t* const* lattices, uint32_t n, const
         base += htp[act];
     }
     hpb[K] = base;
-    if (!runner_maps_ok(hd, htp, hpb, hact, n, K)) return LAT_ESTATE;
+    if (!runner_maps_ok(hd, htp, hpb, hact, n, K, (uint32_t)kMultiThreads)) return LAT_ESTATE;
     std::memset(hctl, 0, sizeof(MultiCtl));
     hctl->total = base;
     hctl->nphases = K;
